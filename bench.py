@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the tvcut hot path: a cold-started AAR solve of one grid to
+the iteration at which its cut first equals the exact (max-flow) minimum.
+
+One step = cold start + k* AAR iterations (FP32 iterates, one check at the
+end) + the cut, with inputs resident in HBM; k* is found once, untimed, by
+checking every iteration against the oracle's min-cut value E* (computed in
+the CPU-baseline leg).  value = vertices x iterations / time (Mvertex-iter/s),
+summed over ranks (replicas: the single-grid path does not shard).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload volume256|seg1024]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1503_01563_gb300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    # 3D 6-connected 256^3 blob volume, integer-scaled LLR unary, weights U{1..30}
+    "volume256": dict(dims=(256, 256, 256), seed=3, cap=1500),
+    # 2D 4-connected 1024^2 blob segmentation, integer-scaled LLR unary and contrast weights
+    "seg1024": dict(dims=(1024, 1024), seed=2, cap=3000),
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def make_problem(name):
+    wl = WORKLOADS[name]
+    if len(wl["dims"]) == 3:
+        return inputs.volume_problem(wl["dims"], wl["seed"])
+    return inputs.segmentation_problem(wl["dims"], wl["seed"])
+
+
+def sweep_bytes_per_vertex(ndim):
+    """Algorithmic bytes per vertex of each sweep kind (FP32 state and weights):
+    first: read z_0, w, a_0; write P, y_0.  middle: read z_k, a_k, P; write P,
+    y_k.  last: read z_last, a_last, P, y_0..y_{r-2}; write every z_k.  A check
+    iteration's last sweep also reads w and writes x (+8 B)."""
+    first = 5 * 4
+    mid = 5 * 4
+    last = (3 + (ndim - 1)) * 4 + ndim * 4
+    return first, mid, last
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_traffic(kind_name, workload):
+    """DRAM bytes per launch of a sweep kernel from a committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = hashlib.sha256(open(os.path.join(ROOT, "paper_1503_01563_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
+    ent = d.get(workload, {}).get(kind_name)
+    if not ent or d.get("sweep_cu_sha256") != src:
+        return None
+    return ent
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_leg(name, w, a, budget_s=12.0):
+    """Oracle (FP64 AAR with its taut-string prox, OpenMP over chains) on the
+    host cores, timed on a bounded sample: whole-grid iterations until the
+    time budget is spent; plus the oracle's exact min-cut value E*."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    e_star = oracle.maxflow(w, a, 1)[1]
+    t_mf = time.perf_counter() - t0
+    n = int(np.prod(w.shape))
+    s = oracle.cold_state(oracle.AAR, w)
+    iters, t_it = 0, 0.0
+    while t_it < budget_s and iters < 200:
+        t0 = time.perf_counter()
+        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+        t_it += time.perf_counter() - t0
+        iters += 1
+    value = n * iters / t_it / 1e6
+    return e_star, {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
+                    "sample": f"{iters} FP64 AAR iterations over the full {name} grid ({t_it:.1f} s), "
+                              f"OpenMP over chains; max-flow E* took {t_mf:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w, a = make_problem(args.workload)
+    n = int(np.prod(w.shape))
+    cores = os.cpu_count() or 1
+    s = oracle.cold_state(oracle.AAR, w)
+    for _ in range(args.warmup):
+        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e6
+    out = {"impl": "reference", "metric": "Mvertex-iter/s", "value": value, "unit": "Mvertex-iter/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "dims": list(WORKLOADS[args.workload]["dims"]),
+                      "algo": "AAR", "step": "one whole-grid AAR iteration of the CPU oracle"},
+           "cpu_baseline": {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} whole-grid FP64 AAR iterations"},
+           "e2e": {"value": value, "unit": "Mvertex-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1503_01563_gb300 import tvcut
+
+    w, a = make_problem(args.workload)
+    dims = tuple(w.shape)
+    n = int(np.prod(dims))
+    ndim = len(dims)
+
+    # CPU leg (rank 0): oracle E* and the oracle's own throughput
+    e_star, cpu_base = None, None
+    if rank == 0:
+        e_star, cpu_base = cpu_leg(args.workload, w, a, budget_s=args.cpu_budget)
+
+    stream = torch.cuda.current_stream(dev)
+    wd = torch.from_numpy(w).to(dev)
+    ad = [torch.from_numpy(x).to(dev) for x in a]
+
+    # find k*: first iteration whose cut energy equals E* (untimed, checks every iteration)
+    kstar = None
+    cap = WORKLOADS[args.workload]["cap"]
+    if rank == 0:
+        probe = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+        probe.set_problem(wd, ad)
+        for k in range(1, cap + 1):
+            _, st = probe.iterate(1)
+            if st.energy_i64 == e_star:
+                kstar = k
+                break
+        probe.close()
+    iters = kstar if kstar else cap
+    if world > 1:
+        t = torch.tensor([iters], device=dev)
+        dist.broadcast(t, 0)
+        iters = int(t.item())
+
+    solver = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    solver.set_problem(wd, ad)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        tvcut.tvcut_reset(solver.h)
+        _, st = solver.iterate(iters)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    tvcut.tvcut_profile(solver.h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms = 0.0
+    energies = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        st = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        energies.append(st.energy_i64)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kms, klaunch = tvcut.tvcut_profile_read(solver.h)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * n * iters * args.steps / (total_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (largest device-time share among sweeps)
+    kinds = ["sweep_first", "sweep_mid", "sweep_last", "check", "other"]
+    bpv = dict(zip(kinds[:3], sweep_bytes_per_vertex(ndim)))
+    dom = max(range(3), key=lambda k: kms[k])
+    dom_name = kinds[dom]
+    launches = int(klaunch[dom])
+    alg_bytes = bpv[dom_name] * n
+    if dom_name == "sweep_last":
+        alg_bytes += 8 * n * args.steps / max(launches, 1)      # one checked iteration per step
+    avg_s = kms[dom] / 1e3 / max(launches, 1)
+    achieved = alg_bytes / avg_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = sweep_traffic(dom_name, args.workload)
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
+                "share_of_step": float(kms[dom] / max(kms.sum(), 1e-9)),
+                "all_sweeps_GBps": float(sum(bpv[kinds[k]] * n * klaunch[k] for k in range(3)) /
+                                         max(sum(kms[:3]) / 1e3, 1e-12) / 1e9)}
+
+    # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
+    e2e_solver = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    labels = np.empty(dims, dtype=np.uint8)
+    w_pin = torch.from_numpy(w).pin_memory()
+    a_pin = [torch.from_numpy(x).pin_memory() for x in a]
+    h2d = int(w.nbytes + sum(x.nbytes for x in a))
+    d2h = int(labels.nbytes)
+    e2e_steps = max(1, args.steps // 2)
+    e2e_s = 0.0
+    for i in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_solver.set_problem(w_pin, a_pin)
+        e2e_solver.iterate(iters)
+        _, st2 = e2e_solver.cut()
+        if i > 0:                       # first call warms the path
+            e2e_s += time.perf_counter() - t0
+    e2e_value = world * n * iters * e2e_steps / e2e_s / 1e6
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "Mvertex-iter/s", "value": value, "unit": "Mvertex-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "dims": list(dims), "algo": "AAR", "iterate": "f32",
+                       "iters_per_step": iters, "step": "cold start + iterations to the oracle-equal cut + cut",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MB buffer written between steps"},
+            "time_to_oracle_equal_cut_ms": {"cold": ms_per_step if kstar else None, "warm": None},
+            "iters_to_oracle_equal_cut": kstar, "oracle_min_cut": e_star,
+            "step_energies_match": all(e == e_star for e in energies),
+            "roofline": roofline, "cpu_baseline": cpu_base,
+            "e2e": {"value": e2e_value, "unit": "Mvertex-iter/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk, "gpu_launches": int(klaunch.sum()),
+            "kernel_ms": dict(zip(kinds, [float(x) for x in kms])),
+            "kernel_launches": dict(zip(kinds, [int(x) for x in klaunch])),
+        }
+        print(json.dumps(out), flush=True)
+    solver.close()
+    e2e_solver.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="volume256")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

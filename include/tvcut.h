@@ -1,0 +1,203 @@
+/*
+ * tvcut -- exact minimum cuts of submodular pairwise grid energies on one
+ * GB300 GPU, by total-variation denoising and product-space projection
+ * methods, after "Convex Optimization for Parallel Energy Minimization"
+ * (Kumar, Barbero, Jegelka, Sra, Bach).
+ *
+ * Problem (Sec. 2, Eq. 1-2 and problem (D)): on a 2D 4-connected or 3D
+ * 6-connected grid with n vertices, find labels l in {0,1}^n minimising
+ *     E(l) = sum_e a_e [l_i != l_j] - sum_i w_i l_i ,    a_e >= 0,
+ * where every undirected grid edge e = (i, j) is counted once.  Label 1 is
+ * favoured where w_i > 0 (the paper's sign: E = f(x) - w^T x).
+ *
+ * Method (Sec. 2.3-4): solve the TV-denoising problem
+ *     min_x f(x) + 1/2 ||x - w||^2 ,   f(x) = sum_e a_e |x_i - x_j| ,
+ * by splitting f into one block of chains per grid axis (Sec. 3.1) and running
+ * averaged alternating reflections (Eq. 3) or alternating projections
+ * (Sec. 4.2) in the product space; every projection onto a block is an exact
+ * weighted 1D-TV prox on each of its chains (Sec. 3.2).  The labels are the
+ * thresholded primal, l_i = [x_i > threshold] with threshold 0 by default
+ * (Sec. 2.3).
+ *
+ * Layout.  Grids are row-major with the LAST axis fastest (numpy order):
+ * dims = {H, W} or {D, H, W}, vertex (i_0, .., i_{ndim-1}) at flat index
+ * sum_k i_k * prod(dims[k+1:]).  Edge weights along axis k are one array in
+ * "compact" layout: the grid's shape with dims[k]-1 along axis k, entry
+ * (.., i_k, ..) being the weight of the edge between (.., i_k, ..) and
+ * (.., i_k + 1, ..).  Product-space states hold ndim arrays of n values, the
+ * block of axis k at offset k*n.
+ *
+ * Memory and streams.  Every handle owns its device buffers.  Input pointers
+ * are read during the call and never retained; output buffers belong to the
+ * caller.  `space` says whether a pointer is host (TVCUT_HOST) or device
+ * (TVCUT_DEVICE) memory.  All work is ordered on the stream given at
+ * creation (NULL = the legacy default stream); calls that return results to
+ * the host synchronise that stream.
+ *
+ * Errors.  Every call returns a tvcut_status; no exception or abort crosses
+ * the ABI.  tvcut_last_error(h) describes the last failure on h (or, with
+ * h == NULL, the last failure of a call without a valid handle on this
+ * thread).  A handle is not thread-safe.
+ */
+#ifndef TVCUT_H
+#define TVCUT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tvcut_ctx* tvcut_t;
+
+typedef enum {
+    TVCUT_OK = 0,
+    TVCUT_NOT_CONVERGED = 1,   /* max_iters reached without a stop criterion */
+    TVCUT_ERR_INVALID = -1,    /* bad argument or input value */
+    TVCUT_ERR_CUDA = -2,       /* a CUDA call failed (message has details) */
+    TVCUT_ERR_OOM = -3,        /* device allocation failed */
+    TVCUT_ERR_STATE = -4,      /* call out of order (e.g. iterate before inputs) */
+    TVCUT_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up */
+} tvcut_status;
+
+enum { TVCUT_I32 = 0, TVCUT_F32 = 1, TVCUT_F64 = 2 };    /* element types */
+enum { TVCUT_HOST = 0, TVCUT_DEVICE = 1 };                /* pointer space */
+enum { TVCUT_AAR = 0, TVCUT_AP = 1 };                     /* algorithms    */
+
+typedef struct {
+    int algo;            /* TVCUT_AAR (Eq. 3, default) or TVCUT_AP (Sec. 4.2) */
+    int iterate_dtype;   /* TVCUT_F32 (default) or TVCUT_F64: precision of the
+                            state and of the chain prox; gaps and energies are
+                            always accumulated in FP64 (and int64 for exact
+                            integer energies) */
+    int check_every;     /* evaluate labels, energy and gaps every k
+                            iterations (default 10; the last iteration of each
+                            tvcut_iterate call is always evaluated) */
+    int mapping;         /* chain-to-thread mapping: -1 = automatic */
+    double gap_tol;      /* stop when the TV duality gap f(x) - y^T x
+                            (Sec. 2.3) is <= gap_tol; 0 disables (default) */
+    double threshold;    /* labels are [x_i > threshold] (default 0) */
+    int reserved[8];     /* must be zero */
+} tvcut_params;
+
+typedef struct {
+    int64_t iters;         /* iterations run since the last cold start */
+    double energy;         /* E(l) of the current labels (FP64 sum) */
+    int64_t energy_i64;    /* E(l) in exact integer arithmetic; valid when
+                              energy_exact != 0 */
+    int energy_exact;      /* unary and all weights were set as TVCUT_I32 */
+    int certified;         /* energy_exact and energy - discrete_lb < 1: with
+                              integer data the labels are then a minimum cut
+                              (Sec. 2.2 certificate; FP32 iterates make the
+                              lower bound approximate, see discrete_lb) */
+    double discrete_lb;    /* sum_i min(y_i - w_i, 0) = -sum_i max(x_i, 0) with
+                              y = w - x, the dual bound of problem (C) (Sec. 2.2);
+                              a true lower bound on E* when y lies in K */
+    double tv_value;       /* f(x) */
+    double tv_gap;         /* f(x) - y^T x, the TV duality gap (Sec. 2.3) */
+    double x_absmax;       /* max_i |x_i| */
+    int64_t n_label1;      /* number of vertices labelled 1 */
+    int64_t reserved[4];
+} tvcut_stats;
+
+/* Fill *p with the defaults listed above. */
+void tvcut_default_params(tvcut_params* p);
+
+/* Create a solver for one grid.  ndim is 2 or 3; dims[k] >= 1.  p may be
+ * NULL (defaults).  cuda_stream is a cudaStream_t or NULL.  Allocates the
+ * device state (about (2 ndim + 4) n values of the iterate type plus n
+ * bytes).  Errors: INVALID (bad ndim/dims/params), OOM, CUDA. */
+tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_params* p,
+                          void* cuda_stream, tvcut_t* out);
+
+/* Release every device buffer of h (h may be NULL). */
+void tvcut_destroy(tvcut_t h);
+
+/* Message of the last failure on h (h == NULL: this thread's last failure
+ * without a handle).  The string stays valid until the next call on h. */
+const char* tvcut_last_error(tvcut_t h);
+
+/* Set the unary terms w (n values in grid layout).  dtype TVCUT_I32,
+ * TVCUT_F32 or TVCUT_F64.  Values must be finite; with an FP32 iterate,
+ * integers must satisfy |w_i| <= 2^24 so that they stay exact.
+ * Resets the iteration state to a cold start. Errors: INVALID, CUDA. */
+tvcut_status tvcut_set_unary(tvcut_t h, const void* w, int dtype, int space);
+
+/* Set the edge weights along grid axis `axis` (0 <= axis < ndim) in compact
+ * layout (see above).  Values must be finite and >= 0 (submodularity, Eq. 2);
+ * the same 2^24 rule applies to integers with an FP32 iterate.  Resets the
+ * iteration state to a cold start.  Errors: INVALID, CUDA. */
+tvcut_status tvcut_set_weights(tvcut_t h, int axis, const void* a, int dtype,
+                               int space);
+
+/* Cold start: AAR z = 0, AP lambda_k = w / ndim (the projection of 0 onto the
+ * consensus set L of Eq. dualdec).  Errors: STATE (no unary yet), CUDA. */
+tvcut_status tvcut_reset(tvcut_t h);
+
+/* Run up to max_iters iterations (max_iters >= 1).  Every check_every
+ * iterations and after the last one, the primal x = w - sum_k y_k of the
+ * current shadow (Eq. dualA, Sec. 2.3) is thresholded and its energy and
+ * gaps are evaluated; iteration stops early when `certified` holds or the TV
+ * gap reaches gap_tol.  Returns OK when a criterion held, NOT_CONVERGED when
+ * max_iters ran out, STATE if unary or weights are missing, CUDA on device
+ * errors.  out (may be NULL) receives the statistics of the last check. */
+tvcut_status tvcut_iterate(tvcut_t h, int64_t max_iters, tvcut_stats* out);
+
+/* Labels of the latest primal (computed from the current state when no
+ * check has run since the last change): labels[i] = [x_i > threshold] for
+ * the n vertices, uint8, written to `labels` in `space` (labels may be NULL
+ * to get statistics only).  out (may be NULL) receives energy and gaps.
+ * Errors: STATE, INVALID, CUDA. */
+tvcut_status tvcut_cut(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out);
+
+/* Copy the latest primal x (n values) out as TVCUT_F32 or TVCUT_F64. */
+tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int space);
+
+/* Copy the product-space state (ndim*n values of the iterate type: z for AAR,
+ * lambda for AP) out of / into the handle: checkpoint, resume, and the warm
+ * start of Sec. 4.4 (reuse the state of a similar, earlier problem). */
+tvcut_status tvcut_get_state(tvcut_t h, void* s, int space);
+tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
+
+/* Warm start from a predicted primal xhat (n FP32 values): every block gets
+ * s_k = (w - xhat)/ndim + tau * xhat.  (With tau = 0 the blocks split w - xhat
+ * evenly; tau > 0 adds the drift that the AAR iterates acquire, Sec. 4.3.)
+ * Errors: STATE, INVALID, CUDA. */
+tvcut_status tvcut_warmstart_primal(tvcut_t h, const float* xhat, float tau,
+                                    int space);
+
+/* Stateless chain operator on device arrays: for every chain along `axis` of
+ * a grid with the given dims, computes the exact weighted 1D-TV prox
+ * (Sec. 3.2) of v with the compact weights a (what = 1: out = prox(v)) or the
+ * projection onto that block's polytope (what = 0: out = v - prox(v), Sec.
+ * 2.3 and 3.3).  v, a, out are DEVICE pointers of dtype TVCUT_F32 or
+ * TVCUT_F64 (all the same); out may equal v.  Allocates nothing; ordered on
+ * `cuda_stream`; does not synchronise.  Errors: INVALID, CUDA (launch). */
+tvcut_status tvcut_project_chains(int ndim, const int64_t* dims, int axis,
+                                  const void* v, const void* a, void* out,
+                                  int dtype, int what, void* cuda_stream);
+
+/* Tracing.  Kernel kinds counted and timed per handle. */
+enum {
+    TVCUT_K_SWEEP_FIRST = 0,   /* chain sweep of block 0 (projection + running sum) */
+    TVCUT_K_SWEEP_MID = 1,     /* chain sweep of a middle block (3D only) */
+    TVCUT_K_SWEEP_LAST = 2,    /* last chain sweep with the fused reflection/averaging update */
+    TVCUT_K_CHECK = 3,         /* threshold + energy + gap evaluation and its reduction */
+    TVCUT_K_OTHER = 4,         /* conversions, cold/warm starts */
+    TVCUT_NKINDS = 5
+};
+
+/* enable != 0: bracket every later kernel launch of h with CUDA events on
+ * h's stream and accumulate device time per kind; 0: stop.  Either way the
+ * accumulated times and launch counts are reset.  Errors: INVALID, CUDA. */
+tvcut_status tvcut_profile(tvcut_t h, int enable);
+
+/* Read the accumulators: ms[TVCUT_NKINDS] (device milliseconds, only while
+ * profiling) and launches[TVCUT_NKINDS] (kernel launches since the last
+ * tvcut_profile call; counted always).  Synchronises h's stream. */
+tvcut_status tvcut_profile_read(tvcut_t h, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVCUT_H */

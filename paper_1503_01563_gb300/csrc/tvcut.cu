@@ -1,0 +1,611 @@
+// C-ABI of tvcut (declared in include/tvcut.h): handle, device buffers and
+// the iteration driver of the product-space methods (Sec. 4.2-4.3).
+//
+// One iteration with r = ndim blocks is r chain sweeps (sweep.cu): sweeps
+// 0..r-2 project their block and accumulate a per-vertex running sum P; the
+// last sweep projects block r-1 and applies the reflection/averaging update
+// to every block state in the same pass.  With AAR (Eq. 3 and Eq. dualA),
+//   z_k <- y_k + (w - 2 sum_j y_j + sum_j z_j) / r ,   y = Pi_K(z),
+// and with AP (Sec. 4.2), lambda_k <- y_k + (w - sum_j y_j) / r.  On check
+// iterations the last sweep also writes the primal x = w - sum_k y_k, which
+// the check kernels (aux.cu) threshold and evaluate.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "tvcut_internal.cuh"
+
+using namespace tvcut;
+
+struct tvcut_ctx {
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t n = 0;
+    tvcut_params p;
+    cudaStream_t stream = nullptr;
+    int esize = 4;                 // bytes of the iterate type
+    void* state = nullptr;         // ndim * n
+    void* w = nullptr;             // n
+    void* a[3] = {nullptr, nullptr, nullptr};
+    int64_t a_len[3] = {0, 0, 0};
+    void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
+    uint8_t* labels = nullptr;     // n
+    CheckPartial* partials = nullptr;
+    DevStatus* dstatus = nullptr;
+    DevStatus* hstatus = nullptr;  // pinned
+    bool have_w = false, have_a[3] = {false, false, false};
+    bool int_w = false, int_a[3] = {false, false, false};
+    bool x_valid = false, labels_valid = false;
+    int64_t iters = 0;
+    tvcut_stats last;
+    std::string err;
+    // tracing: launch counts per kernel kind, and (when enabled) device time
+    // from CUDA events recorded around each launch on the handle's stream
+    bool prof = false;
+    double prof_ms[TVCUT_NKINDS] = {0, 0, 0, 0, 0};
+    int64_t launches[TVCUT_NKINDS] = {0, 0, 0, 0, 0};
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+static thread_local std::string g_err;
+
+static tvcut_status fail(tvcut_t h, tvcut_status st, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_err = msg;
+    return st;
+}
+
+static tvcut_status cuda_fail(tvcut_t h, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? TVCUT_ERR_OOM : TVCUT_ERR_CUDA, m);
+}
+
+#define CK(h, expr, where)                                  \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+extern "C" void tvcut_default_params(tvcut_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->algo = TVCUT_AAR;
+    p->iterate_dtype = TVCUT_F32;
+    p->check_every = 10;
+    p->mapping = -1;
+    p->gap_tol = 0.0;
+    p->threshold = 0.0;
+}
+
+extern "C" const char* tvcut_last_error(tvcut_t h)
+{
+    return h ? h->err.c_str() : g_err.c_str();
+}
+
+extern "C" void tvcut_destroy(tvcut_t h)
+{
+    if (!h) return;
+    cudaFree(h->state);
+    cudaFree(h->w);
+    for (int k = 0; k < 3; ++k) cudaFree(h->a[k]);
+    cudaFree(h->scratch);
+    cudaFree(h->labels);
+    cudaFree(h->partials);
+    cudaFree(h->dstatus);
+    cudaFreeHost(h->hstatus);
+    for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+static bool valid_params(const tvcut_params* p, std::string& why)
+{
+    if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP) { why = "params.algo must be TVCUT_AAR or TVCUT_AP"; return false; }
+    if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
+    if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
+    if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
+    if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
+    for (int i = 0; i < 8; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
+    return true;
+}
+
+extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_params* p,
+                                     void* cuda_stream, tvcut_t* out)
+{
+    if (!out) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: out is NULL");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: ndim must be 2 or 3");
+    if (!dims) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: dims is NULL");
+    int64_t n = 1;
+    for (int k = 0; k < ndim; ++k) {
+        if (dims[k] < 1 || dims[k] > (int64_t)1 << 30)
+            return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: every dims[k] must be in [1, 2^30]");
+        n *= dims[k];
+        if (n > ((int64_t)1 << 40)) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: grid too large");
+    }
+    tvcut_params prm;
+    tvcut_default_params(&prm);
+    if (p) prm = *p;
+    std::string why;
+    if (!valid_params(&prm, why)) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: " + why);
+
+    tvcut_t h = new tvcut_ctx();
+    h->ndim = ndim;
+    for (int k = 0; k < ndim; ++k) h->dims[k] = dims[k];
+    h->n = n;
+    h->p = prm;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->esize = prm.iterate_dtype == TVCUT_F64 ? 8 : 4;
+    memset(&h->last, 0, sizeof(h->last));
+    const size_t es = (size_t)h->esize;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&h->state, es * (size_t)(ndim * n));
+    if (e == cudaSuccess) e = cudaMalloc(&h->w, es * (size_t)n);
+    for (int k = 0; k < ndim && e == cudaSuccess; ++k) {
+        h->a_len[k] = n / dims[k] * (dims[k] - 1);
+        e = cudaMalloc(&h->a[k], es * (size_t)(h->a_len[k] > 0 ? h->a_len[k] : 1));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->labels, (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(CheckPartial) * kCheckBlocks);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->dstatus, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->hstatus, sizeof(DevStatus));
+    if (e != cudaSuccess) {
+        tvcut_status st = cuda_fail(nullptr, e, "tvcut_create: allocation");
+        tvcut_destroy(h);
+        return st;
+    }
+    *out = h;
+    return TVCUT_OK;
+}
+
+// ---- typed helpers --------------------------------------------------------
+
+template <typename T>
+static T* P_of(tvcut_t h) { return (T*)h->scratch; }
+template <typename T>
+static T* X_of(tvcut_t h) { return (T*)h->scratch + h->n; }
+template <typename T>
+static T* S_of(tvcut_t h, int k) { return (T*)h->state + (int64_t)k * h->n; }
+
+// ---- tracing ----------------------------------------------------------------
+
+static cudaError_t take_event(tvcut_t h, cudaEvent_t* e)
+{
+    if (!h->ev_pool.empty()) {
+        *e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+}
+
+// Launch `nk` kernels through `fn` as one traced group of kind `kind`.
+template <class F>
+static cudaError_t traced(tvcut_t h, int kind, int nk, F&& fn)
+{
+    h->launches[kind] += nk;
+    if (!h->prof) return fn();
+    cudaEvent_t a, b;
+    cudaError_t e = take_event(h, &a);
+    if (e == cudaSuccess) e = take_event(h, &b);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(a, h->stream);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+    h->pending.push_back({kind, a, b});
+    return e;
+}
+
+// Accumulate the pending event pairs; call only after the stream synchronised.
+static cudaError_t flush_trace(tvcut_t h)
+{
+    cudaError_t err = cudaSuccess;
+    for (auto& p : h->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e == cudaSuccess) h->prof_ms[p.kind] += ms;
+        else if (err == cudaSuccess) err = e;
+        h->ev_pool.push_back(p.a);
+        h->ev_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    return err;
+}
+
+static size_t dtype_size(int dt)
+{
+    return dt == TVCUT_F64 ? 8 : 4;
+}
+
+// Bring a caller array (host or device) into `dst` (iterate type), validating.
+template <typename T>
+static tvcut_status ingest(tvcut_t h, const void* src, int dtype, int space, int64_t count,
+                           bool nonneg, T* dst, const char* what)
+{
+    if (dtype != TVCUT_I32 && dtype != TVCUT_F32 && dtype != TVCUT_F64)
+        return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": dtype must be TVCUT_I32, TVCUT_F32 or TVCUT_F64");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE)
+        return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": space must be TVCUT_HOST or TVCUT_DEVICE");
+    if (count > 0 && !src) return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": NULL data");
+    const void* dsrc = src;
+    if (space == TVCUT_HOST && count > 0) {
+        // staging in the scratch area (2n iterate values >= count * 8 bytes)
+        CK(h, cudaMemcpyAsync(h->scratch, src, dtype_size(dtype) * (size_t)count, cudaMemcpyHostToDevice, h->stream), what);
+        dsrc = h->scratch;
+    }
+    int* dflags = &h->dstatus->flags;
+    CK(h, cudaMemsetAsync(dflags, 0, sizeof(int), h->stream), what);
+    if (count > 0)
+        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_convert<T>(dsrc, dtype, dst, count, nonneg, dflags, h->stream); }), what);
+    CK(h, cudaMemcpyAsync(&h->hstatus->flags, dflags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), what);
+    CK(h, cudaStreamSynchronize(h->stream), what);
+    CK(h, flush_trace(h), what);
+    const int f = h->hstatus->flags;
+    if (f & FLAG_NONFINITE) return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": non-finite value");
+    if (f & FLAG_NEGATIVE) return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": negative edge weight (energy not submodular)");
+    if (f & FLAG_INEXACT) return fail(h, TVCUT_ERR_INVALID, std::string(what) + ": integer too large to be exact in the iterate type (|v| <= 2^24 for FP32)");
+    return TVCUT_OK;
+}
+
+template <typename T>
+static tvcut_status cold_start(tvcut_t h)
+{
+    if (h->p.algo == TVCUT_AP) {
+        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_cold_ap<T>((const T*)h->w, (T*)h->state, h->ndim, h->n, h->stream); }),
+           "cold start");
+    } else {
+        CK(h, cudaMemsetAsync(h->state, 0, (size_t)h->esize * (size_t)(h->ndim * h->n), h->stream), "cold start");
+    }
+    h->iters = 0;
+    h->x_valid = h->labels_valid = false;
+    return TVCUT_OK;
+}
+
+static bool inputs_ready(tvcut_t h)
+{
+    if (!h->have_w) return false;
+    for (int k = 0; k < h->ndim; ++k) if (!h->have_a[k]) return false;
+    return true;
+}
+
+// One pass over the blocks.  mode_first/mid/last select the epilogues.
+template <typename T>
+static cudaError_t run_sweeps(tvcut_t h, int first, int mid, int last, int check)
+{
+    const int r = h->ndim;
+    for (int k = 0; k < r; ++k) {
+        SweepArgs<T> A;
+        memset(&A, 0, sizeof(A));
+        A.g = chain_geom(h->ndim, h->dims, k);
+        A.v = S_of<T>(h, k);
+        A.a = (const T*)h->a[k];
+        A.out = S_of<T>(h, k);
+        A.P = P_of<T>(h);
+        A.w = (const T*)h->w;
+        for (int j = 0; j < r; ++j) A.Z[j] = S_of<T>(h, j);
+        A.x = X_of<T>(h);
+        A.r = r;
+        A.check = check;
+        const int mode = k == 0 ? first : (k == r - 1 ? last : mid);
+        const int kind = k == 0 ? TVCUT_K_SWEEP_FIRST : (k == r - 1 ? TVCUT_K_SWEEP_LAST : TVCUT_K_SWEEP_MID);
+        cudaError_t e = traced(h, kind, 1, [&] { return launch_sweep<T>(mode, A, h->stream); });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static tvcut_status run_check(tvcut_t h)
+{
+    CheckArgs<T> C;
+    memset(&C, 0, sizeof(C));
+    C.ndim = h->ndim;
+    C.n = h->n;
+    for (int k = 0; k < h->ndim; ++k) {
+        C.dims[k] = h->dims[k];
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        C.inner[k] = g.inner;
+        C.a[k] = (const T*)h->a[k];
+    }
+    C.x = X_of<T>(h);
+    C.w = (const T*)h->w;
+    C.labels = h->labels;
+    C.threshold = (T)h->p.threshold;
+    C.partials = h->partials;
+    CK(h, traced(h, TVCUT_K_CHECK, 2, [&] { return launch_check<T>(C, h->dstatus, h->stream); }), "check");
+    CK(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream), "check");
+    CK(h, cudaStreamSynchronize(h->stream), "check");
+    CK(h, flush_trace(h), "check");
+    const CheckPartial& s = h->hstatus->sum;
+    tvcut_stats& st = h->last;
+    memset(&st, 0, sizeof(st));
+    st.iters = h->iters;
+    st.energy = s.energy;
+    st.energy_i64 = s.energy_i;
+    bool exact = h->int_w;
+    for (int k = 0; k < h->ndim; ++k) exact = exact && h->int_a[k];
+    st.energy_exact = exact ? 1 : 0;
+    st.discrete_lb = s.lb;
+    st.tv_value = s.tv;
+    st.tv_gap = s.tv - s.ytx;
+    st.x_absmax = s.xabs;
+    st.n_label1 = s.n1;
+    st.certified = (exact && (double)s.energy_i - s.lb < 1.0) ? 1 : 0;
+    h->labels_valid = true;
+    return TVCUT_OK;
+}
+
+template <typename T>
+static tvcut_status ensure_primal(tvcut_t h)
+{
+    if (h->x_valid) return TVCUT_OK;
+    CK(h, run_sweeps<T>(h, MODE_EVAL_FIRST, MODE_EVAL_MID, MODE_EVAL_LAST, 1), "evaluate primal");
+    h->x_valid = true;
+    h->labels_valid = false;
+    return TVCUT_OK;
+}
+
+template <typename T>
+static tvcut_status iterate_impl(tvcut_t h, int64_t max_iters, tvcut_stats* out)
+{
+    const bool aar = h->p.algo == TVCUT_AAR;
+    const int first = aar ? MODE_AAR_FIRST : MODE_AP_FIRST;
+    const int mid = aar ? MODE_AAR_MID : MODE_AP_MID;
+    const int last = aar ? MODE_AAR_LAST : MODE_AP_LAST;
+    tvcut_status ret = TVCUT_NOT_CONVERGED;
+    for (int64_t it = 0; it < max_iters; ++it) {
+        const bool check = ((h->iters + 1) % h->p.check_every == 0) || it == max_iters - 1;
+        CK(h, run_sweeps<T>(h, first, mid, last, check ? 1 : 0), "iterate");
+        h->iters += 1;
+        h->x_valid = false;
+        h->labels_valid = false;
+        if (check) {
+            h->x_valid = true;
+            tvcut_status st = run_check<T>(h);
+            if (st != TVCUT_OK) return st;
+            const tvcut_stats& s = h->last;
+            if (s.certified || (h->p.gap_tol > 0.0 && s.tv_gap <= h->p.gap_tol)) {
+                ret = TVCUT_OK;
+                break;
+            }
+        }
+    }
+    if (out) *out = h->last;
+    return ret;
+}
+
+// ---- C-ABI entry points ----------------------------------------------------
+
+#define DISPATCH(h, FN, ...) ((h)->esize == 8 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
+
+template <typename T>
+static tvcut_status set_unary_impl(tvcut_t h, const void* w, int dtype, int space)
+{
+    tvcut_status st = ingest<T>(h, w, dtype, space, h->n, false, (T*)h->w, "tvcut_set_unary");
+    if (st != TVCUT_OK) { h->have_w = false; return st; }
+    h->have_w = true;
+    h->int_w = dtype == TVCUT_I32;
+    return cold_start<T>(h);
+}
+
+extern "C" tvcut_status tvcut_set_unary(tvcut_t h, const void* w, int dtype, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_set_unary: NULL handle");
+    return DISPATCH(h, set_unary_impl, h, w, dtype, space);
+}
+
+template <typename T>
+static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dtype, int space)
+{
+    tvcut_status st = ingest<T>(h, a, dtype, space, h->a_len[axis], true, (T*)h->a[axis], "tvcut_set_weights");
+    if (st != TVCUT_OK) { h->have_a[axis] = false; return st; }
+    h->have_a[axis] = true;
+    h->int_a[axis] = dtype == TVCUT_I32;
+    if (h->have_w) return cold_start<T>(h);
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_set_weights(tvcut_t h, int axis, const void* a, int dtype, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_set_weights: NULL handle");
+    if (axis < 0 || axis >= h->ndim) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_weights: axis out of range");
+    return DISPATCH(h, set_weights_impl, h, axis, a, dtype, space);
+}
+
+extern "C" tvcut_status tvcut_reset(tvcut_t h)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_reset: NULL handle");
+    if (!h->have_w) return fail(h, TVCUT_ERR_STATE, "tvcut_reset: unary not set");
+    return DISPATCH(h, cold_start, h);
+}
+
+extern "C" tvcut_status tvcut_iterate(tvcut_t h, int64_t max_iters, tvcut_stats* out)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_iterate: NULL handle");
+    if (max_iters < 1) return fail(h, TVCUT_ERR_INVALID, "tvcut_iterate: max_iters must be >= 1");
+    if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_iterate: unary and all edge weights must be set first");
+    return DISPATCH(h, iterate_impl, h, max_iters, out);
+}
+
+template <typename T>
+static tvcut_status cut_impl(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out)
+{
+    if (!h->labels_valid) {
+        tvcut_status st = ensure_primal<T>(h);
+        if (st != TVCUT_OK) return st;
+        st = run_check<T>(h);
+        if (st != TVCUT_OK) return st;
+    }
+    if (labels) {
+        CK(h, cudaMemcpyAsync(labels, h->labels, (size_t)h->n,
+                              space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
+           "tvcut_cut");
+        CK(h, cudaStreamSynchronize(h->stream), "tvcut_cut");
+    }
+    if (out) *out = h->last;
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_cut(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_cut: NULL handle");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_cut: bad space");
+    if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_cut: unary and all edge weights must be set first");
+    return DISPATCH(h, cut_impl, h, labels, space, out);
+}
+
+template <typename T>
+static tvcut_status get_primal_impl(tvcut_t h, void* x, int dtype, int space)
+{
+    tvcut_status st = ensure_primal<T>(h);
+    if (st != TVCUT_OK) return st;
+    const size_t bytes = dtype_size(dtype) * (size_t)h->n;
+    if (space == TVCUT_DEVICE) {
+        CK(h, launch_convert_out<T>(X_of<T>(h), x, dtype, h->n, h->stream), "tvcut_get_primal");
+        CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_primal");
+        return TVCUT_OK;
+    }
+    if ((size_t)dtype_size(dtype) == sizeof(T)) {
+        CK(h, cudaMemcpyAsync(x, X_of<T>(h), bytes, cudaMemcpyDeviceToHost, h->stream), "tvcut_get_primal");
+        CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_primal");
+        return TVCUT_OK;
+    }
+    // other element type: copy out in the iterate type, then widen/narrow
+    std::vector<T> tmp((size_t)h->n);
+    CK(h, cudaMemcpyAsync(tmp.data(), X_of<T>(h), sizeof(T) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream),
+       "tvcut_get_primal");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_primal");
+    if (dtype == TVCUT_F64) for (int64_t i = 0; i < h->n; ++i) ((double*)x)[i] = (double)tmp[(size_t)i];
+    else for (int64_t i = 0; i < h->n; ++i) ((float*)x)[i] = (float)tmp[(size_t)i];
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_get_primal: NULL handle");
+    if (!x) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_primal: NULL output");
+    if (dtype != TVCUT_F32 && dtype != TVCUT_F64) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_primal: dtype must be F32 or F64");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_primal: bad space");
+    if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_get_primal: unary and all edge weights must be set first");
+    return DISPATCH(h, get_primal_impl, h, x, dtype, space);
+}
+
+extern "C" tvcut_status tvcut_get_state(tvcut_t h, void* s, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_get_state: NULL handle");
+    if (!s) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: NULL output");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: bad space");
+    CK(h, cudaMemcpyAsync(s, h->state, (size_t)h->esize * (size_t)(h->ndim * h->n),
+                          space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
+       "tvcut_get_state");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_state");
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_set_state: NULL handle");
+    if (!s) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_state: NULL input");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_state: bad space");
+    CK(h, cudaMemcpyAsync(h->state, s, (size_t)h->esize * (size_t)(h->ndim * h->n),
+                          space == TVCUT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
+       "tvcut_set_state");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_set_state");
+    h->x_valid = h->labels_valid = false;
+    return TVCUT_OK;
+}
+
+template <typename T>
+static tvcut_status warmstart_impl(tvcut_t h, const float* xhat, float tau, int space)
+{
+    const float* d = xhat;
+    if (space == TVCUT_HOST) {
+        CK(h, cudaMemcpyAsync(h->scratch, xhat, sizeof(float) * (size_t)h->n, cudaMemcpyHostToDevice, h->stream),
+           "tvcut_warmstart_primal");
+        d = (const float*)h->scratch;
+    }
+    // the kernel reads xhat[i] before writing state; state and scratch are disjoint
+    CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_warmstart<T>((const T*)h->w, d, tau, (T*)h->state, h->ndim, h->n, h->stream); }),
+       "tvcut_warmstart_primal");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_warmstart_primal");
+    h->x_valid = h->labels_valid = false;
+    h->iters = 0;
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_warmstart_primal(tvcut_t h, const float* xhat, float tau, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_warmstart_primal: NULL handle");
+    if (!xhat) return fail(h, TVCUT_ERR_INVALID, "tvcut_warmstart_primal: NULL xhat");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_warmstart_primal: bad space");
+    if (!(tau == tau)) return fail(h, TVCUT_ERR_INVALID, "tvcut_warmstart_primal: tau is NaN");
+    if (!h->have_w) return fail(h, TVCUT_ERR_STATE, "tvcut_warmstart_primal: unary not set");
+    return DISPATCH(h, warmstart_impl, h, xhat, tau, space);
+}
+
+template <typename T>
+static tvcut_status project_impl(int ndim, const int64_t* dims, int axis, const void* v, const void* a,
+                                 void* out, int what, cudaStream_t s)
+{
+    SweepArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    A.g = chain_geom(ndim, dims, axis);
+    A.v = (const T*)v;
+    A.a = (const T*)a;
+    A.out = (T*)out;
+    cudaError_t e = launch_sweep<T>(what == 1 ? MODE_PROX : MODE_PROJ, A, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tvcut_project_chains");
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_project_chains(int ndim, const int64_t* dims, int axis, const void* v,
+                                             const void* a, void* out, int dtype, int what,
+                                             void* cuda_stream)
+{
+    if (ndim < 1 || ndim > 3 || !dims) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: ndim must be 1..3");
+    if (axis < 0 || axis >= ndim) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: axis out of range");
+    if (what != 0 && what != 1) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: what must be 0 or 1");
+    int64_t n = 1;
+    for (int k = 0; k < ndim; ++k) {
+        if (dims[k] < 1 || dims[k] > (int64_t)1 << 30) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: bad dims");
+        n *= dims[k];
+    }
+    if (!v || !out || (!a && dims[axis] > 1)) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: NULL pointer");
+    if (dtype == TVCUT_F32) return project_impl<float>(ndim, dims, axis, v, a, out, what, (cudaStream_t)cuda_stream);
+    if (dtype == TVCUT_F64) return project_impl<double>(ndim, dims, axis, v, a, out, what, (cudaStream_t)cuda_stream);
+    return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_project_chains: dtype must be TVCUT_F32 or TVCUT_F64");
+}
+
+extern "C" tvcut_status tvcut_profile(tvcut_t h, int enable)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_profile: NULL handle");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_profile");
+    CK(h, flush_trace(h), "tvcut_profile");
+    h->prof = enable != 0;
+    for (int k = 0; k < TVCUT_NKINDS; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->launches[k] = 0;
+    }
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_profile_read(tvcut_t h, double* ms, int64_t* launches)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_profile_read: NULL handle");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_profile_read");
+    CK(h, flush_trace(h), "tvcut_profile_read");
+    for (int k = 0; k < TVCUT_NKINDS; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->launches[k];
+    }
+    return TVCUT_OK;
+}

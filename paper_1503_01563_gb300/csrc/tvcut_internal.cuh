@@ -1,0 +1,112 @@
+// Internal declarations shared by the tvcut CUDA translation units.
+// Not part of the public ABI (see include/tvcut.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tvcut.h"
+
+namespace tvcut {
+
+// Chains of one grid axis k: chain c = (o, q) with o < outer = prod(dims[:k])
+// and q < inner = prod(dims[k+1:]); element j of chain c sits at
+// o*m*inner + q + j*inner, the weight of its edge (j, j+1) at
+// o*(m-1)*inner + q + j*inner (compact layout).
+struct ChainGeom {
+    int64_t outer;
+    int64_t inner;
+    int64_t nchains;
+    int m;
+};
+
+// Per-element epilogues of one chain sweep (what is done with y = v - prox(v)).
+enum SweepMode : int {
+    MODE_PROJ = 0,      // out = y
+    MODE_PROX = 1,      // out = x = prox(v)
+    MODE_AAR_FIRST = 2, // P = w + v - 2y; block state <- y
+    MODE_AAR_MID = 3,   // P += v - 2y;   block state <- y
+    MODE_AAR_LAST = 4,  // c = (P + v - 2y)/r; z_k <- y_k + c for all k; x = w - sum y
+    MODE_AP_FIRST = 5,  // P = w - y;      block state <- y
+    MODE_AP_MID = 6,    // P -= y;         block state <- y
+    MODE_AP_LAST = 7,   // c = (P - y)/r;  lambda_k <- y_k + c; x = P - y
+    MODE_EVAL_FIRST = 8,// P = w - y       (state untouched)
+    MODE_EVAL_MID = 9,  // P -= y
+    MODE_EVAL_LAST = 10,// x = P - y
+};
+
+template <typename T>
+struct SweepArgs {
+    ChainGeom g;
+    const T* v;        // chain input (block state or standalone input)
+    const T* a;        // compact weights of the chain axis
+    T* out;            // PROJ/PROX output, or the block state written with y
+    T* P;              // running per-vertex sum across the blocks of one iteration
+    const T* w;        // unary
+    T* Z[3];           // block states (LAST modes update all of them)
+    T* x;              // primal output (LAST modes when check != 0)
+    int r;             // number of blocks
+    int check;         // LAST modes: also write x
+};
+
+// FP64/int64 partial sums of one check (energy, bounds, gaps).
+struct CheckPartial {
+    double energy;
+    double lb;
+    double tv;
+    double ytx;
+    double xabs;
+    long long energy_i;
+    long long n1;
+    long long pad;
+};
+
+struct DevStatus {
+    CheckPartial sum;
+    int flags;          // validation flags of the last conversion
+    int pad[15];
+};
+
+template <typename T>
+struct CheckArgs {
+    int ndim;
+    int64_t dims[3];
+    int64_t inner[3];
+    int64_t n;
+    const T* x;
+    const T* w;
+    const T* a[3];
+    uint8_t* labels;
+    T threshold;
+    CheckPartial* partials;
+};
+
+// Validation flags raised by the conversion kernels.
+enum : int {
+    FLAG_NONFINITE = 1,
+    FLAG_NEGATIVE = 2,
+    FLAG_INEXACT = 4,   // integer too large to be exact in the iterate type
+};
+
+// Launchers (sweep.cu)
+template <typename T>
+cudaError_t launch_sweep(int mode, const SweepArgs<T>& args, cudaStream_t s);
+
+// Launchers (aux.cu)
+constexpr int kCheckBlocks = 608;     // 4 x 152 SMs
+constexpr int kCheckThreads = 256;
+template <typename T>
+cudaError_t launch_check(const CheckArgs<T>& args, DevStatus* status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(const void* src, int src_dtype, T* dst, int64_t n, bool nonneg,
+                           int* flags, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert_out(const T* src, void* dst, int dst_dtype, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cold_ap(const T* w, T* state, int r, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state, int r,
+                             int64_t n, cudaStream_t s);
+
+ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
+
+}  // namespace tvcut

@@ -1,0 +1,309 @@
+"""Python binding of the tvcut C-ABI (include/tvcut.h).
+
+Argument marshalling only: every step of the solver runs in libtvcut.so's
+CUDA kernels.  Functions carry the C names (``tvcut_create`` ...); ``Solver``
+wraps a handle for convenience.  Arrays may be numpy arrays (host memory) or
+CUDA torch tensors (device memory); the binding passes their pointers and the
+matching ``space`` flag.  There is no fallback: if libtvcut.so is missing the
+import-time load raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtvcut.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_TIMEOUT = -1, -2, -3, -4, -5
+I32, F32, F64 = 0, 1, 2
+HOST, DEVICE = 0, 1
+AAR, AP = 0, 1
+
+EXPORTED = [
+    "tvcut_default_params", "tvcut_create", "tvcut_destroy", "tvcut_last_error",
+    "tvcut_set_unary", "tvcut_set_weights", "tvcut_reset", "tvcut_iterate", "tvcut_cut",
+    "tvcut_get_primal", "tvcut_get_state", "tvcut_set_state", "tvcut_warmstart_primal",
+    "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read",
+]
+K_SWEEP_FIRST, K_SWEEP_MID, K_SWEEP_LAST, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4, 5
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("algo", ctypes.c_int),
+        ("iterate_dtype", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("mapping", ctypes.c_int),
+        ("gap_tol", ctypes.c_double),
+        ("threshold", ctypes.c_double),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int64),
+        ("energy", ctypes.c_double),
+        ("energy_i64", ctypes.c_int64),
+        ("energy_exact", ctypes.c_int),
+        ("certified", ctypes.c_int),
+        ("discrete_lb", ctypes.c_double),
+        ("tv_value", ctypes.c_double),
+        ("tv_gap", ctypes.c_double),
+        ("x_absmax", ctypes.c_double),
+        ("n_label1", ctypes.c_int64),
+        ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class TvcutError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tvcut error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libtvcut.so not built ({path}); run paper_1503_01563_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    c_int = ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "tvcut_default_params": (None, [ctypes.POINTER(Params)]),
+        "tvcut_create": (st, [c_int, P, ctypes.POINTER(Params), P, ctypes.POINTER(P)]),
+        "tvcut_destroy": (None, [P]),
+        "tvcut_last_error": (ctypes.c_char_p, [P]),
+        "tvcut_set_unary": (st, [P, P, c_int, c_int]),
+        "tvcut_set_weights": (st, [P, c_int, P, c_int, c_int]),
+        "tvcut_reset": (st, [P]),
+        "tvcut_iterate": (st, [P, i64, ctypes.POINTER(Stats)]),
+        "tvcut_cut": (st, [P, P, c_int, ctypes.POINTER(Stats)]),
+        "tvcut_get_primal": (st, [P, P, c_int, c_int]),
+        "tvcut_get_state": (st, [P, P, c_int]),
+        "tvcut_set_state": (st, [P, P, c_int]),
+        "tvcut_warmstart_primal": (st, [P, P, ctypes.c_float, c_int]),
+        "tvcut_project_chains": (st, [c_int, P, c_int, P, P, P, c_int, c_int, P]),
+        "tvcut_profile": (st, [P, c_int]),
+        "tvcut_profile_read": (st, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+# ---- marshalling helpers ----------------------------------------------------
+
+def _dtype_code(dt) -> int:
+    dt = str(dt)
+    if dt.endswith("int32"):
+        return I32
+    if dt.endswith("float32"):
+        return F32
+    if dt.endswith("float64"):
+        return F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def _buf(arr):
+    """(pointer, space, dtype code, keepalive) of a numpy array or torch tensor."""
+    if isinstance(arr, np.ndarray):
+        arr = np.ascontiguousarray(arr)
+        return ctypes.c_void_p(arr.ctypes.data), HOST, _dtype_code(arr.dtype), arr
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(arr, torch.Tensor):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        space = DEVICE if arr.is_cuda else HOST
+        return ctypes.c_void_p(arr.data_ptr()), space, _dtype_code(arr.dtype), arr
+    arr = np.ascontiguousarray(np.asarray(arr))
+    return ctypes.c_void_p(arr.ctypes.data), HOST, _dtype_code(arr.dtype), arr
+
+
+def _check(code, h=None):
+    if code < 0:
+        msg = lib().tvcut_last_error(h)
+        raise TvcutError(code, msg.decode() if msg else "")
+    return code
+
+
+def tvcut_default_params() -> Params:
+    p = Params()
+    lib().tvcut_default_params(ctypes.byref(p))
+    return p
+
+
+def tvcut_create(dims, params: Params | None = None, stream=None):
+    dims_arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    h = ctypes.c_void_p()
+    s = ctypes.c_void_p(int(stream) if stream else 0)
+    _check(lib().tvcut_create(len(dims), dims_arr, ctypes.byref(params) if params else None, s, ctypes.byref(h)))
+    return h
+
+
+def tvcut_destroy(h):
+    lib().tvcut_destroy(h)
+
+
+def tvcut_set_unary(h, w):
+    p, space, dt, keep = _buf(w)
+    return _check(lib().tvcut_set_unary(h, p, dt, space), h)
+
+
+def tvcut_set_weights(h, axis, a):
+    p, space, dt, keep = _buf(a)
+    return _check(lib().tvcut_set_weights(h, int(axis), p, dt, space), h)
+
+
+def tvcut_reset(h):
+    return _check(lib().tvcut_reset(h), h)
+
+
+def tvcut_iterate(h, max_iters):
+    st = Stats()
+    code = _check(lib().tvcut_iterate(h, int(max_iters), ctypes.byref(st)), h)
+    return code, st
+
+
+def tvcut_cut(h, labels=None):
+    """labels: None, a uint8 numpy array (host) or a uint8 CUDA tensor."""
+    st = Stats()
+    if labels is None:
+        _check(lib().tvcut_cut(h, None, HOST, ctypes.byref(st)), h)
+    elif isinstance(labels, np.ndarray):
+        assert labels.dtype == np.uint8 and labels.flags.c_contiguous
+        _check(lib().tvcut_cut(h, ctypes.c_void_p(labels.ctypes.data), HOST, ctypes.byref(st)), h)
+    else:
+        _check(lib().tvcut_cut(h, ctypes.c_void_p(labels.data_ptr()), DEVICE if labels.is_cuda else HOST,
+                               ctypes.byref(st)), h)
+    return st
+
+
+def tvcut_get_primal(h, out):
+    p, space, dt, keep = _buf(out)
+    return _check(lib().tvcut_get_primal(h, p, dt, space), h)
+
+
+def tvcut_get_state(h, out):
+    p, space, dt, keep = _buf(out)
+    return _check(lib().tvcut_get_state(h, p, space), h)
+
+
+def tvcut_set_state(h, s):
+    p, space, dt, keep = _buf(s)
+    return _check(lib().tvcut_set_state(h, p, space), h)
+
+
+def tvcut_warmstart_primal(h, xhat, tau: float):
+    p, space, dt, keep = _buf(xhat)
+    if dt != F32:
+        raise TypeError("xhat must be float32")
+    return _check(lib().tvcut_warmstart_primal(h, p, ctypes.c_float(tau), space), h)
+
+
+def tvcut_project_chains(dims, axis, v, a, out, what=0, stream=None):
+    """Device tensors only (float32 or float64)."""
+    dims_arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    pv, sv, dv, _ = _buf(v)
+    pa, sa, da, _ = _buf(a)
+    po, so, do, _ = _buf(out)
+    if not (sv == sa == so == DEVICE):
+        raise ValueError("tvcut_project_chains takes device tensors")
+    s = ctypes.c_void_p(int(stream) if stream else 0)
+    return _check(lib().tvcut_project_chains(len(dims), dims_arr, int(axis), pv, pa, po, dv, int(what), s))
+
+
+def tvcut_profile(h, enable: bool):
+    return _check(lib().tvcut_profile(h, 1 if enable else 0), h)
+
+
+def tvcut_profile_read(h):
+    """Returns (ms per kernel kind, launches per kernel kind) as numpy arrays."""
+    ms = np.zeros(NKINDS, dtype=np.float64)
+    n = np.zeros(NKINDS, dtype=np.int64)
+    _check(lib().tvcut_profile_read(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(n.ctypes.data)), h)
+    return ms, n
+
+
+class Solver:
+    """One grid: ``Solver(dims, algo=AAR, dtype=F32)``; ``set_problem(w, a)``;
+    ``iterate(k)``; ``cut()``."""
+
+    def __init__(self, dims, algo=AAR, dtype=F32, check_every=10, gap_tol=0.0, threshold=0.0,
+                 stream=None):
+        p = tvcut_default_params()
+        p.algo = algo
+        p.iterate_dtype = dtype
+        p.check_every = check_every
+        p.gap_tol = gap_tol
+        p.threshold = threshold
+        self.dims = tuple(int(d) for d in dims)
+        self.n = int(np.prod(self.dims))
+        self.dtype = dtype
+        self.h = tvcut_create(self.dims, p, stream)
+
+    def close(self):
+        if self.h:
+            tvcut_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_problem(self, w, a):
+        tvcut_set_unary(self.h, w)
+        for k, ak in enumerate(a):
+            tvcut_set_weights(self.h, k, ak)
+
+    def reset(self):
+        tvcut_reset(self.h)
+
+    def iterate(self, max_iters):
+        return tvcut_iterate(self.h, max_iters)
+
+    def cut(self, labels=True):
+        if labels:
+            lab = np.empty(self.dims, dtype=np.uint8)
+            st = tvcut_cut(self.h, lab)
+            return lab, st
+        return None, tvcut_cut(self.h, None)
+
+    def primal(self, dtype=np.float64):
+        x = np.empty(self.dims, dtype=dtype)
+        tvcut_get_primal(self.h, x)
+        return x
+
+    def state(self):
+        s = np.empty((len(self.dims),) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
+        tvcut_get_state(self.h, s)
+        return s
+
+    def set_state(self, s):
+        want = np.float64 if self.dtype == F64 else np.float32
+        tvcut_set_state(self.h, np.ascontiguousarray(s, dtype=want))

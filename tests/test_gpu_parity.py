@@ -1,0 +1,289 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Tolerances: FP64 iterate mode agrees with the FP64 oracle to 1e-9 relative
+(same mathematics, different summation order); FP32 iterates agree with the
+FP64 oracle to 1e-4 of max|x| (max-abs, relative) after the same number of
+iterations; cut energies on integer data are compared exactly.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1503_01563_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NPROC = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def tv():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_01563_gb300 import tvcut
+    tvcut.lib()
+    return tvcut
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rel_err(got, want):
+    return float(np.abs(np.asarray(got, np.float64) - want).max() / max(1.0, np.abs(want).max()))
+
+
+# ---- the chain operator (Sec. 3.2) ----------------------------------------------
+
+CHAIN_CASES = [((1, 1), 1), ((3, 1), 1), ((5, 2), 1), ((4, 3), 1), ((6, 31), 1), ((40, 33), 0),
+               ((257, 7), 0), ((9, 1000), 1), ((5, 6, 7), 0), ((5, 6, 7), 1), ((5, 6, 7), 2),
+               ((3, 4, 256), 2), ((64, 2, 3), 0)]
+
+
+@pytest.mark.parametrize("dims,axis", CHAIN_CASES)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_project_chains(tv, orc, dims, axis, dtype):
+    g = np.random.default_rng(hash((dims, axis)) % 2**32)
+    v = g.normal(0, 10, size=dims)
+    v += np.cumsum(g.integers(-1, 2, size=dims) * 5.0, axis=axis)   # piecewise structure
+    a = g.uniform(0, 4, size=inputs.compact_shape(dims, axis))
+    a[g.random(a.shape) < 0.1] = 0.0
+    want = orc.project_block(v, a, axis)
+    want_x = v - want
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    code = tv.F64 if dtype == "f64" else tv.F32
+    vd, ad = dev(v, tdt), dev(a, tdt)
+    out = torch.empty_like(vd)
+    tv.tvcut_project_chains(dims, axis, vd, ad, out, what=0)
+    torch.cuda.synchronize()
+    tol = 1e-9 if dtype == "f64" else 2e-5
+    scale = max(1.0, np.abs(v).max())
+    assert np.abs(out.cpu().numpy() - want).max() <= tol * scale
+    out2 = torch.empty_like(vd)
+    tv.tvcut_project_chains(dims, axis, vd, ad, out2, what=1)
+    torch.cuda.synchronize()
+    assert np.abs(out2.cpu().numpy() - want_x).max() <= tol * scale
+    # in place is allowed
+    vd2 = vd.clone()
+    tv.tvcut_project_chains(dims, axis, vd2, ad, vd2, what=0)
+    torch.cuda.synchronize()
+    assert torch.equal(vd2, out)
+    _ = code
+
+
+def test_project_chains_large_values(tv, orc):
+    """The drifting AAR iterates reach |z| >> a; the chain prox must stay
+    accurate relative to the input scale."""
+    g = np.random.default_rng(3)
+    dims = (16, 300)
+    v = 5000.0 + g.normal(0, 3, size=dims) + np.repeat(g.normal(0, 500, size=(16, 6)), 50, axis=1)
+    a = g.uniform(0, 10, size=(16, 299))
+    want = orc.project_block(v, a, 1)
+    for tdt, tol in [(torch.float64, 1e-11), (torch.float32, 1e-6)]:
+        vd, ad = dev(v, tdt), dev(a, tdt)
+        out = torch.empty_like(vd)
+        tv.tvcut_project_chains(dims, 1, vd, ad, out, what=0)
+        torch.cuda.synchronize()
+        assert np.abs(out.cpu().numpy() - want).max() <= tol * np.abs(v).max()
+
+
+# ---- iterations (Sec. 4.2-4.3) ---------------------------------------------------
+
+ITER_CASES = [(64, 64), (37, 53), (1, 9), (9, 1), (2, 2), (13, 17, 19), (1, 5, 6), (7, 1, 3)]
+
+
+@pytest.mark.parametrize("dims", ITER_CASES)
+@pytest.mark.parametrize("algo", [0, 1])
+def test_iterations_f64(tv, orc, dims, algo):
+    w, a = inputs.uniform_grid(dims, 11)
+    k = 17
+    s = tv.Solver(dims, algo=algo, dtype=tv.F64, check_every=1000)
+    s.set_problem(w, a)
+    s.iterate(k)
+    ref_s, ref_x = orc.iterate(algo, w, a, orc.cold_state(algo, w), k)
+    assert rel_err(s.state(), ref_s) < 1e-9
+    assert rel_err(s.primal(), ref_x) < 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("dims", [(64, 64), (37, 53), (13, 17, 19)])
+@pytest.mark.parametrize("algo", [0, 1])
+def test_iterations_f32(tv, orc, dims, algo):
+    w, a = inputs.uniform_grid(dims, 12)
+    s = tv.Solver(dims, algo=algo, dtype=tv.F32, check_every=1000)
+    s.set_problem(dev(w), [dev(x) for x in a])
+    st = orc.cold_state(algo, w)
+    done = 0
+    for k in (1, 10, 50):
+        s.iterate(k - done)
+        st, x = orc.iterate(algo, w, a, st, k - done)
+        done = k
+        assert rel_err(s.primal(), x) < 1e-4, k
+        assert rel_err(s.state(), st) < 1e-4, k
+    s.close()
+
+
+def test_check_statistics(tv, orc):
+    """Energy, bounds and gaps of a check equal the oracle's on the same x."""
+    dims = (31, 29)
+    w, a = inputs.uniform_grid(dims, 5)
+    s = tv.Solver(dims, dtype=tv.F64, check_every=1)
+    s.set_problem(w, a)
+    for k in (1, 7, 40):
+        _, st = s.iterate(k)
+        lab, st2 = s.cut()
+        x = s.primal()
+        assert np.array_equal(lab, (x > 0).astype(np.uint8))
+        e = orc.energy(w, a, lab)
+        assert st.energy_exact == 1 and st.energy_i64 == e and st2.energy_i64 == e
+        assert abs(st.energy - e) < 1e-6
+        y = w - x
+        assert abs(st.discrete_lb - np.minimum(y - w, 0).sum()) < 1e-6 * max(1, abs(st.discrete_lb))
+        f = orc.tv_value(a, x)
+        assert abs(st.tv_value - f) < 1e-8 * max(1, f)
+        assert abs(st.tv_gap - (f - (y * x).sum())) < 1e-6 * max(1, f)
+        assert st.n_label1 == int(lab.sum())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_cut_64(tv, orc, seed):
+    """64x64, w in [-50, 50], a in [1, 20]: the FP64 GPU cut energy equals the
+    max-flow minimum exactly (Sec. 2.3 thresholding)."""
+    dims = (64, 64)
+    w, a = inputs.uniform_grid(dims, seed)
+    e_star, smin, smax = orc.min_cut(w, a)
+    # threshold 1/(2n): with integer data a nonzero |x*_i| is at least 1/n
+    s = tv.Solver(dims, dtype=tv.F64, check_every=5, threshold=0.5 / w.size)
+    s.set_problem(w, a)
+    code, st = s.iterate(20000)
+    assert code == tv.OK and st.certified
+    lab, st = s.cut()
+    assert st.energy_i64 == e_star
+    assert orc.energy(w, a, lab) == e_star
+    # every minimiser lies between the minimal and maximal ones (Sec. 2.1)
+    assert np.all(lab >= smin) and np.all(lab <= smax)
+    s.close()
+
+
+@pytest.mark.parametrize("dims", [(4, 4), (3, 3, 2)])
+def test_exact_cut_bruteforce(tv, orc, dims):
+    for seed in range(10):
+        w, a = inputs.uniform_grid(dims, seed)
+        e, _, _, _ = orc.bruteforce(w, a)
+        for dt in (tv.F64, tv.F32):
+            s = tv.Solver(dims, dtype=dt, check_every=1, threshold=0.5 / w.size)
+            s.set_problem(w, a)
+            s.iterate(5000)
+            _, st = s.cut()
+            assert st.energy_i64 == e, (seed, dt)
+            s.close()
+
+
+def test_exact_cut_3d(tv, orc):
+    dims = (12, 14, 16)
+    w, a = inputs.uniform_grid(dims, 3)
+    e_star = orc.maxflow(w, a)[1]
+    s = tv.Solver(dims, dtype=tv.F64, check_every=5, threshold=0.5 / w.size)
+    s.set_problem(w, a)
+    code, st = s.iterate(20000)
+    assert code == tv.OK and st.energy_i64 == e_star
+
+
+def test_zero_weights(tv):
+    dims = (5, 8)
+    w, a = inputs.uniform_grid(dims, 2)
+    a = [np.zeros_like(x) for x in a]
+    s = tv.Solver(dims, dtype=tv.F64, check_every=1)
+    s.set_problem(w, a)
+    s.iterate(1)
+    np.testing.assert_array_equal(s.primal(), w)
+
+
+def test_state_roundtrip_and_warm_start(tv, orc):
+    dims = (20, 24)
+    w, a = inputs.uniform_grid(dims, 9)
+    s = tv.Solver(dims, dtype=tv.F64, check_every=1000)
+    s.set_problem(w, a)
+    s.iterate(30)
+    z = s.state()
+    s.iterate(5)
+    z35 = s.state()
+    s.set_state(z)
+    s.iterate(5)
+    np.testing.assert_array_equal(s.state(), z35)
+    # warm start: s_k = (w - xhat)/r + tau xhat
+    xhat = np.linspace(-1, 1, w.size).reshape(dims).astype(np.float32)
+    tv.tvcut_warmstart_primal(s.h, xhat, 0.25)
+    want = (w - xhat.astype(np.float64)) / 2 + 0.25 * xhat.astype(np.float64)
+    st = s.state()
+    np.testing.assert_allclose(st[0], want, atol=1e-12)
+    np.testing.assert_allclose(st[1], want, atol=1e-12)
+
+
+def test_errors(tv):
+    dims = (6, 7)
+    w, a = inputs.uniform_grid(dims, 1)
+    s = tv.Solver(dims)
+    with pytest.raises(tv.TvcutError) as e:
+        s.iterate(3)
+    assert e.value.code == tv.ERR_STATE
+    tv.tvcut_set_unary(s.h, w)
+    with pytest.raises(tv.TvcutError) as e:
+        s.iterate(3)
+    assert e.value.code == tv.ERR_STATE
+    bad = a[0].copy()
+    bad[0, 0] = -1
+    with pytest.raises(tv.TvcutError) as e:
+        tv.tvcut_set_weights(s.h, 0, bad)
+    assert e.value.code == tv.ERR_INVALID
+    wn = w.astype(np.float32)
+    wn[1, 1] = np.nan
+    with pytest.raises(tv.TvcutError) as e:
+        tv.tvcut_set_unary(s.h, wn)
+    assert e.value.code == tv.ERR_INVALID
+    big = w.copy()
+    big[0, 0] = 2 ** 24 + 1
+    with pytest.raises(tv.TvcutError) as e:
+        tv.tvcut_set_unary(s.h, big)
+    assert e.value.code == tv.ERR_INVALID
+    with pytest.raises(tv.TvcutError):
+        tv.tvcut_set_weights(s.h, 2, a[0])
+    s.set_problem(w, a)
+    code, st = s.iterate(2)
+    assert code == tv.NOT_CONVERGED
+    s.close()
+
+
+# ---- full-size workloads, in the configuration the benchmark times ---------------
+
+def test_full_size_2d_segmentation(tv, orc):
+    """1024x1024 blob segmentation, FP32 iterates: the whole primal after a
+    few iterations agrees with the FP64 oracle."""
+    dims = (1024, 1024)
+    w, a = inputs.segmentation_problem(dims, 2)
+    s = tv.Solver(dims, dtype=tv.F32, check_every=1000)
+    s.set_problem(dev(w), [dev(x) for x in a])
+    s.iterate(4)
+    _, x = orc.iterate(0, w, a, orc.cold_state(0, w), 4, nthreads=NPROC)
+    assert rel_err(s.primal(), x) < 1e-4
+    s.close()
+
+
+def test_full_size_3d_volume(tv, orc):
+    """256^3 blob volume, FP32 iterates, two iterations against the oracle."""
+    dims = (256, 256, 256)
+    w, a = inputs.volume_problem(dims, 3)
+    s = tv.Solver(dims, dtype=tv.F32, check_every=1000)
+    s.set_problem(dev(w), [dev(x) for x in a])
+    s.iterate(2)
+    _, x = orc.iterate(0, w, a, orc.cold_state(0, w), 2, nthreads=NPROC)
+    assert rel_err(s.primal(), x) < 1e-4
+    _, st = s.cut(labels=False)
+    lab = (s.primal() > 0).astype(np.uint8)
+    assert st.energy_i64 == int(orc.energy(w, a, lab))
+    s.close()
