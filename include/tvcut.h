@@ -73,11 +73,22 @@ typedef struct {
     int check_every;     /* evaluate labels, energy and gaps every k
                             iterations (default 10; the last iteration of each
                             tvcut_iterate call is always evaluated) */
-    int mapping;         /* chain-to-thread mapping: -1 = automatic */
+    int mapping;         /* chain-to-thread mapping of the sweeps: -1 automatic
+                            (default); 0 one thread per chain reading global
+                            memory; 1, 2, 3 shared-memory tiles of 8, 16, 32
+                            chains (falls back to 0 when a tile does not fit) */
     double gap_tol;      /* stop when the TV duality gap f(x) - y^T x
                             (Sec. 2.3) is <= gap_tol; 0 disables (default) */
     double threshold;    /* labels are [x_i > threshold] (default 0) */
-    int reserved[8];     /* must be zero */
+    int level_sets;      /* L >= 0: each check also evaluates the level sets
+                            [x_i > threshold +- S 10^-j], j = 2..L+1, S = max|w|,
+                            and keeps the lowest-energy one.  Sec. 2.1: every
+                            level set of a solution of the relaxation solves
+                            (D); near convergence this removes the arbitrary
+                            signs of iterates on regions where x* is exactly 0.
+                            Default 8 (at most 8); 0 thresholds at `threshold`
+                            only */
+    int reserved[7];     /* must be zero */
 } tvcut_params;
 
 typedef struct {
@@ -97,7 +108,8 @@ typedef struct {
     double tv_gap;         /* f(x) - y^T x, the TV duality gap (Sec. 2.3) */
     double x_absmax;       /* max_i |x_i| */
     int64_t n_label1;      /* number of vertices labelled 1 */
-    int64_t reserved[4];
+    double threshold;      /* level at which the labels were cut */
+    int64_t reserved[3];
 } tvcut_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -144,8 +156,8 @@ tvcut_status tvcut_reset(tvcut_t h);
 tvcut_status tvcut_iterate(tvcut_t h, int64_t max_iters, tvcut_stats* out);
 
 /* Labels of the latest primal (computed from the current state when no
- * check has run since the last change): labels[i] = [x_i > threshold] for
- * the n vertices, uint8, written to `labels` in `space` (labels may be NULL
+ * check has run since the last change): labels[i] = [x_i > t] for the n
+ * vertices, t the level chosen by the last check (stats.threshold), uint8, written to `labels` in `space` (labels may be NULL
  * to get statistics only).  out (may be NULL) receives energy and gaps.
  * Errors: STATE, INVALID, CUDA. */
 tvcut_status tvcut_cut(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out);

@@ -103,6 +103,87 @@ __global__ void __launch_bounds__(256) finalize_kernel(const CheckPartial* parti
     if (threadIdx.x == 0) status->sum = r;
 }
 
+// Energies of the level sets [x > levels[j]] (Sec. 2.1: every level set of a
+// solution of the relaxation solves (D)), FP64 and exact int64.
+template <typename T>
+__global__ void __launch_bounds__(kCheckThreads) level_kernel(CheckArgs<T> A)
+{
+    double e[kMaxLevels];
+    long long ei[kMaxLevels];
+    int n1[kMaxLevels];
+#pragma unroll
+    for (int j = 0; j < kMaxLevels; ++j) { e[j] = 0.0; ei[j] = 0; n1[j] = 0; }
+    const int L = A.nlevels;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n; g += stride) {
+        const T xg = A.x[g];
+        const double wg = (double)A.w[g];
+        const long long wi = llrint(wg);
+#pragma unroll
+        for (int j = 0; j < kMaxLevels; ++j)
+            if (j < L && xg > A.levels[j]) { e[j] -= wg; ei[j] -= wi; n1[j] += 1; }
+        for (int k = 0; k < A.ndim; ++k) {
+            const int64_t inner = A.inner[k];
+            const int64_t mk = A.dims[k];
+            const int64_t o = g / (mk * inner);
+            const int64_t jj = (g - o * mk * inner) / inner;
+            if (jj + 1 < mk) {
+                const T x2 = A.x[g + inner];
+                const double ae = (double)A.a[k][g - o * inner];
+                const long long aei = llrint(ae);
+#pragma unroll
+                for (int j = 0; j < kMaxLevels; ++j)
+                    if (j < L && ((xg > A.levels[j]) != (x2 > A.levels[j]))) { e[j] += ae; ei[j] += aei; }
+            }
+        }
+    }
+    // block reduction, one level at a time, fixed order
+    __shared__ double se[kCheckThreads / 32];
+    __shared__ long long sei[kCheckThreads / 32];
+    __shared__ long long sn[kCheckThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kMaxLevels; ++j) {
+        if (j >= L) break;
+        double a = e[j];
+        long long b = ei[j];
+        long long c = n1[j];
+        for (int d = 16; d > 0; d >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, d);
+            b += __shfl_down_sync(0xffffffffu, b, d);
+            c += __shfl_down_sync(0xffffffffu, c, d);
+        }
+        if (lane == 0) { se[wid] = a; sei[wid] = b; sn[wid] = c; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0;
+            long long tb = 0, tc = 0;
+            for (int w = 0; w < kCheckThreads / 32; ++w) { ta += se[w]; tb += sei[w]; tc += sn[w]; }
+            A.level_partials[blockIdx.x].energy[j] = ta;
+            A.level_partials[blockIdx.x].energy_i[j] = tb;
+            A.level_partials[blockIdx.x].n1[j] = tc;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(32) level_finalize_kernel(const LevelPartial* partials, int count, int L,
+                                                            DevStatus* status)
+{
+    const int j = threadIdx.x;
+    if (j >= L) return;
+    double a = 0.0;
+    long long b = 0, c = 0;
+    for (int i = 0; i < count; ++i) {
+        a += partials[i].energy[j];
+        b += partials[i].energy_i[j];
+        c += partials[i].n1[j];
+    }
+    status->levels.energy[j] = a;
+    status->levels.energy_i[j] = b;
+    status->levels.n1[j] = c;
+}
+
 template <typename T>
 cudaError_t launch_check(const CheckArgs<T>& A, DevStatus* status, cudaStream_t s)
 {
@@ -110,15 +191,38 @@ cudaError_t launch_check(const CheckArgs<T>& A, DevStatus* status, cudaStream_t 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_kernel<<<1, 256, 0, s>>>(A.partials, kCheckBlocks, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || A.nlevels <= 0) return e;
+    level_kernel<T><<<kCheckBlocks, kCheckThreads, 0, s>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    level_finalize_kernel<<<1, 32, 0, s>>>(A.level_partials, kCheckBlocks, A.nlevels, status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void labels_kernel(const T* x, T thr, uint8_t* labels, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        labels[i] = (uint8_t)(x[i] > thr);
+}
+
+template <typename T>
+cudaError_t launch_labels(const T* x, T threshold, uint8_t* labels, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    labels_kernel<T><<<kCheckBlocks, kCheckThreads, 0, s>>>(x, threshold, labels, n);
     return cudaGetLastError();
 }
 
 // ---- conversion of caller inputs into the iterate type, with validation ----
 
 template <typename S, typename T>
-__global__ void convert_kernel(const S* src, T* dst, int64_t n, bool nonneg, int* flags)
+__global__ void convert_kernel(const S* src, T* dst, int64_t n, bool nonneg, int* flags, unsigned* absmax_bits)
 {
     int f = 0;
+    float amax = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const S v = src[i];
@@ -130,21 +234,23 @@ __global__ void convert_kernel(const S* src, T* dst, int64_t n, bool nonneg, int
             if ((double)t != d) f |= FLAG_INEXACT;  // integer input not exact in T
         }
         dst[i] = t;
+        amax = fmaxf(amax, fabsf((float)d));
     }
     if (f) atomicOr(flags, f);
+    if (isfinite(amax) && amax > 0.f) atomicMax(absmax_bits, __float_as_uint(amax));   // order-preserving for >= 0
 }
 
 template <typename T>
 cudaError_t launch_convert(const void* src, int src_dtype, T* dst, int64_t n, bool nonneg,
-                           int* flags, cudaStream_t s)
+                           int* flags, unsigned* absmax_bits, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (int)((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
     switch (src_dtype) {
-    case TVCUT_I32: convert_kernel<int32_t, T><<<blocks, threads, 0, s>>>((const int32_t*)src, dst, n, nonneg, flags); break;
-    case TVCUT_F32: convert_kernel<float, T><<<blocks, threads, 0, s>>>((const float*)src, dst, n, nonneg, flags); break;
-    case TVCUT_F64: convert_kernel<double, T><<<blocks, threads, 0, s>>>((const double*)src, dst, n, nonneg, flags); break;
+    case TVCUT_I32: convert_kernel<int32_t, T><<<blocks, threads, 0, s>>>((const int32_t*)src, dst, n, nonneg, flags, absmax_bits); break;
+    case TVCUT_F32: convert_kernel<float, T><<<blocks, threads, 0, s>>>((const float*)src, dst, n, nonneg, flags, absmax_bits); break;
+    case TVCUT_F64: convert_kernel<double, T><<<blocks, threads, 0, s>>>((const double*)src, dst, n, nonneg, flags, absmax_bits); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -217,7 +323,8 @@ cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state,
 
 #define TVCUT_INST(T)                                                                          \
     template cudaError_t launch_check<T>(const CheckArgs<T>&, DevStatus*, cudaStream_t);        \
-    template cudaError_t launch_convert<T>(const void*, int, T*, int64_t, bool, int*, cudaStream_t); \
+    template cudaError_t launch_convert<T>(const void*, int, T*, int64_t, bool, int*, unsigned*, cudaStream_t); \
+    template cudaError_t launch_labels<T>(const T*, T, uint8_t*, int64_t, cudaStream_t);         \
     template cudaError_t launch_convert_out<T>(const T*, void*, int, int64_t, cudaStream_t);    \
     template cudaError_t launch_cold_ap<T>(const T*, T*, int, int64_t, cudaStream_t);           \
     template cudaError_t launch_warmstart<T>(const T*, const float*, float, T*, int, int64_t, cudaStream_t);

@@ -151,10 +151,221 @@ __global__ void __launch_bounds__(128) sweep_global_kernel(SweepArgs<T> A)
     }
 }
 
+// ---- tiled sweep ------------------------------------------------------------
+//
+// One CTA owns NC chains of one axis (a "tile") and stages them whole into
+// shared memory, element-major ([j][lane], padded pitch NC+1 so that both the
+// transposing loads of row chains and the per-lane scan are bank-conflict
+// free).  Three phases separated by barriers:
+//   L: all threads issue asynchronous 4/8-byte copies (cp.async) of the chain
+//      inputs v and the weights a, coalesced along whichever index is
+//      contiguous in global memory, with every copy in flight at once;
+//   S: warp 0 runs the taut-string scan of its lane's chain out of shared
+//      memory; each final segment value is written over the weights of the
+//      same positions, which the scan never reads again;
+//   E: all threads apply the sweep's epilogue element by element from
+//      shared memory (y = v - x), coalesced like phase L.
+// Several CTAs per SM overlap their phases.
+
+constexpr int kTileThreads = 256;
+
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem)
+{
+    if constexpr (sizeof(T) == 8) cp_async_8(smem, gmem);
+    else cp_async_4(smem, gmem);
+}
+
+// Taut-string scan of one chain held in shared memory at sv[j*LD], sa[j*LD];
+// final segment values overwrite sa.
+template <typename T, int LD>
+__device__ __forceinline__ void scan_smem(int m, const T* sv, T* sa)
+{
+    int s = 0, i = 0, ih = 0, il = 0;
+    T u0 = T(0), th = T(0), tl = T(0), uh = T(0), ul = T(0), ah = T(0), al = T(0);
+    for (;;) {
+        const T vi = sv[i * LD];
+        const T Ai = (i < m - 1) ? sa[i * LD] : T(0);
+        if (i == s) {
+            th = vi + Ai - u0;
+            tl = vi - Ai - u0;
+            uh = Ai;
+            ul = -Ai;
+            ih = il = i;
+            ah = al = Ai;
+        } else {
+            uh += th - vi;
+            ul += tl - vi;
+            if (uh < -Ai) {
+                for (int j = s; j <= ih; ++j) sa[j * LD] = th;
+                u0 = ah;
+                s = i = ih + 1;
+                continue;
+            }
+            if (ul > Ai) {
+                for (int j = s; j <= il; ++j) sa[j * LD] = tl;
+                u0 = -al;
+                s = i = il + 1;
+                continue;
+            }
+            const T len = T(i - s + 1);
+            if (uh > Ai) {
+                th -= (uh - Ai) / len;
+                uh = Ai;
+                ih = i;
+                ah = Ai;
+            }
+            if (ul < -Ai) {
+                tl += (-Ai - ul) / len;
+                ul = -Ai;
+                il = i;
+                al = Ai;
+            }
+        }
+        if (i == m - 1) {
+            for (int j = s; j <= m - 1; ++j) sa[j * LD] = th;
+            break;
+        }
+        ++i;
+    }
+}
+
+template <typename T, int MODE, int NC, bool ROWS>
+__global__ void __launch_bounds__(kTileThreads) sweep_tile_kernel(SweepArgs<T> A)
+{
+    constexpr int LD = NC + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sv = (T*)smem_raw;
+    const int m = A.g.m;
+    T* sa = sv + (size_t)m * LD;
+    const int64_t inner = A.g.inner;
+
+    // tile -> first chain; lanes beyond `nvalid` are padding
+    int64_t vbase, abase;     // global offsets of (lane 0, j = 0)
+    int nvalid;
+    if constexpr (ROWS) {
+        const int64_t c0 = (int64_t)blockIdx.x * NC;
+        nvalid = (int)min((int64_t)NC, A.g.nchains - c0);
+        vbase = c0 * m;
+        abase = c0 * (m - 1);
+    } else {
+        const int64_t tiles_per_o = (inner + NC - 1) / NC;
+        const int64_t o = blockIdx.x / tiles_per_o;
+        const int64_t q0 = (blockIdx.x - o * tiles_per_o) * NC;
+        nvalid = (int)min((int64_t)NC, inner - q0);
+        vbase = o * (int64_t)m * inner + q0;
+        abase = o * (int64_t)(m - 1) * inner + q0;
+    }
+    const int total = m * NC;
+
+    // ---- L: stage v and a ----
+    for (int idx = threadIdx.x; idx < total; idx += kTileThreads) {
+        int j, lane;
+        if constexpr (ROWS) { lane = idx / m; j = idx - lane * m; }
+        else { j = idx / NC; lane = idx - j * NC; }
+        T* dv = sv + j * LD + lane;
+        T* da = sa + j * LD + lane;
+        if (lane < nvalid) {
+            const int64_t gv = ROWS ? vbase + (int64_t)lane * m + j : vbase + (int64_t)j * inner + lane;
+            cp_async_elem(dv, A.v + gv);
+            if (j < m - 1) {
+                const int64_t ga = ROWS ? abase + (int64_t)lane * (m - 1) + j : abase + (int64_t)j * inner + lane;
+                cp_async_elem(da, A.a + ga);
+            }
+        } else {
+            *dv = T(0);
+            *da = T(0);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // ---- S: one lane per chain ----
+    if (threadIdx.x < NC && (int)threadIdx.x < nvalid) scan_smem<T, LD>(m, sv + threadIdx.x, sa + threadIdx.x);
+    __syncthreads();
+
+    // ---- E: fused epilogue ----
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < total; idx += kTileThreads) {
+        int j, lane;
+        if constexpr (ROWS) { lane = idx / m; j = idx - lane * m; }
+        else { j = idx / NC; lane = idx - j * NC; }
+        if (lane >= nvalid) continue;
+        const int64_t g = ROWS ? vbase + (int64_t)lane * m + j : vbase + (int64_t)j * inner + lane;
+        epilogue<T, MODE>(A, g, sv[j * LD + lane], sa[j * LD + lane]);
+    }
+}
+
+template <typename T>
+static size_t tile_smem_bytes(int m, int nc)
+{
+    return (size_t)2 * (size_t)m * (size_t)(nc + 1) * sizeof(T);
+}
+
+constexpr size_t kTileSmemLimit = 200 * 1024;
+
+template <typename T, int MODE, int NC, bool ROWS>
+static cudaError_t launch_tile(const SweepArgs<T>& A, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes<T>(A.g.m, NC);
+    static bool attr_set[64] = {};        // per instantiation and device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(sweep_tile_kernel<T, MODE, NC, ROWS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemLimit);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    int64_t tiles;
+    if (ROWS) tiles = (A.g.nchains + NC - 1) / NC;
+    else tiles = A.g.outer * ((A.g.inner + NC - 1) / NC);
+    sweep_tile_kernel<T, MODE, NC, ROWS><<<(unsigned)tiles, kTileThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE, int NC>
+static cudaError_t launch_tile_nc(const SweepArgs<T>& A, cudaStream_t s)
+{
+    if (A.g.inner == 1) return launch_tile<T, MODE, NC, true>(A, s);
+    return launch_tile<T, MODE, NC, false>(A, s);
+}
+
 template <typename T, int MODE>
 static cudaError_t launch_mode(const SweepArgs<T>& A, cudaStream_t s)
 {
     if (A.g.nchains <= 0 || A.g.m <= 0) return cudaSuccess;
+    const int mp = A.mapping;
+    if (mp == 3 && tile_smem_bytes<T>(A.g.m, 32) <= kTileSmemLimit) return launch_tile_nc<T, MODE, 32>(A, s);
+    if (mp == 2 && tile_smem_bytes<T>(A.g.m, 16) <= kTileSmemLimit) return launch_tile_nc<T, MODE, 16>(A, s);
+    if (mp == 1 && tile_smem_bytes<T>(A.g.m, 8) <= kTileSmemLimit) return launch_tile_nc<T, MODE, 8>(A, s);
+    if (mp < 0) {
+        // widest tile that fits the shared-memory budget; the thread-per-chain
+        // global-memory kernel takes chains too long for any tile
+        if (tile_smem_bytes<T>(A.g.m, 32) <= kTileSmemLimit / 2 && A.g.nchains >= 32 * 152)
+            return launch_tile_nc<T, MODE, 32>(A, s);
+        if (tile_smem_bytes<T>(A.g.m, 16) <= kTileSmemLimit)
+            return launch_tile_nc<T, MODE, 16>(A, s);
+        if (tile_smem_bytes<T>(A.g.m, 8) <= kTileSmemLimit)
+            return launch_tile_nc<T, MODE, 8>(A, s);
+    }
     const int threads = 128;
     const int64_t blocks = (A.g.nchains + threads - 1) / threads;
     sweep_global_kernel<T, MODE><<<(unsigned)blocks, threads, 0, s>>>(A);

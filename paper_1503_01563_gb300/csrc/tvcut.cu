@@ -9,6 +9,7 @@
 // and with AP (Sec. 4.2), lambda_k <- y_k + (w - sum_j y_j) / r.  On check
 // iterations the last sweep also writes the primal x = w - sum_k y_k, which
 // the check kernels (aux.cu) threshold and evaluate.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -34,6 +35,8 @@ struct tvcut_ctx {
     void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
     uint8_t* labels = nullptr;     // n
     CheckPartial* partials = nullptr;
+    LevelPartial* level_partials = nullptr;
+    double wmax = 0.0;             // max |w|: scale of the level-set ladder
     DevStatus* dstatus = nullptr;
     DevStatus* hstatus = nullptr;  // pinned
     bool have_w = false, have_a[3] = {false, false, false};
@@ -83,6 +86,7 @@ extern "C" void tvcut_default_params(tvcut_params* p)
     p->mapping = -1;
     p->gap_tol = 0.0;
     p->threshold = 0.0;
+    p->level_sets = 8;
 }
 
 extern "C" const char* tvcut_last_error(tvcut_t h)
@@ -99,6 +103,7 @@ extern "C" void tvcut_destroy(tvcut_t h)
     cudaFree(h->scratch);
     cudaFree(h->labels);
     cudaFree(h->partials);
+    cudaFree(h->level_partials);
     cudaFree(h->dstatus);
     cudaFreeHost(h->hstatus);
     for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -111,9 +116,11 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP) { why = "params.algo must be TVCUT_AAR or TVCUT_AP"; return false; }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
+    if (p->mapping < -1 || p->mapping > 3) { why = "params.mapping must be -1 (auto) or 0..3"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
-    for (int i = 0; i < 8; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
+    if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
+    for (int i = 0; i < 7; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
     return true;
 }
 
@@ -156,6 +163,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->labels, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(CheckPartial) * kCheckBlocks);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->level_partials, sizeof(LevelPartial) * kCheckBlocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->dstatus, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->hstatus, sizeof(DevStatus));
     if (e != cudaSuccess) {
@@ -242,11 +250,13 @@ static tvcut_status ingest(tvcut_t h, const void* src, int dtype, int space, int
         CK(h, cudaMemcpyAsync(h->scratch, src, dtype_size(dtype) * (size_t)count, cudaMemcpyHostToDevice, h->stream), what);
         dsrc = h->scratch;
     }
-    int* dflags = &h->dstatus->flags;
-    CK(h, cudaMemsetAsync(dflags, 0, sizeof(int), h->stream), what);
+    int* dflags = &h->dstatus->flags;       // flags and absmax_bits are adjacent
+    CK(h, cudaMemsetAsync(dflags, 0, 2 * sizeof(int), h->stream), what);
     if (count > 0)
-        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_convert<T>(dsrc, dtype, dst, count, nonneg, dflags, h->stream); }), what);
-    CK(h, cudaMemcpyAsync(&h->hstatus->flags, dflags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), what);
+        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] {
+               return launch_convert<T>(dsrc, dtype, dst, count, nonneg, dflags, &h->dstatus->absmax_bits, h->stream);
+           }), what);
+    CK(h, cudaMemcpyAsync(&h->hstatus->flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream), what);
     CK(h, cudaStreamSynchronize(h->stream), what);
     CK(h, flush_trace(h), what);
     const int f = h->hstatus->flags;
@@ -295,6 +305,7 @@ static cudaError_t run_sweeps(tvcut_t h, int first, int mid, int last, int check
         A.x = X_of<T>(h);
         A.r = r;
         A.check = check;
+        A.mapping = h->p.mapping;
         const int mode = k == 0 ? first : (k == r - 1 ? last : mid);
         const int kind = k == 0 ? TVCUT_K_SWEEP_FIRST : (k == r - 1 ? TVCUT_K_SWEEP_LAST : TVCUT_K_SWEEP_MID);
         cudaError_t e = traced(h, kind, 1, [&] { return launch_sweep<T>(mode, A, h->stream); });
@@ -321,25 +332,55 @@ static tvcut_status run_check(tvcut_t h)
     C.labels = h->labels;
     C.threshold = (T)h->p.threshold;
     C.partials = h->partials;
-    CK(h, traced(h, TVCUT_K_CHECK, 2, [&] { return launch_check<T>(C, h->dstatus, h->stream); }), "check");
+    // level-set ladder: threshold, then threshold +- S 10^-j, j = 2, 3, ...
+    double lv[kMaxLevels];
+    int L = 0;
+    if (h->p.level_sets > 0 && h->wmax > 0.0) {
+        lv[L++] = h->p.threshold;
+        for (int j = 0; j < h->p.level_sets; ++j) {
+            const double d = h->wmax * pow(10.0, -(double)(j + 2));
+            lv[L++] = h->p.threshold + d;
+            lv[L++] = h->p.threshold - d;
+        }
+    }
+    C.nlevels = L;
+    for (int j = 0; j < L; ++j) C.levels[j] = (T)lv[j];
+    C.level_partials = h->level_partials;
+    CK(h, traced(h, TVCUT_K_CHECK, L > 0 ? 4 : 2, [&] { return launch_check<T>(C, h->dstatus, h->stream); }), "check");
     CK(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream), "check");
     CK(h, cudaStreamSynchronize(h->stream), "check");
     CK(h, flush_trace(h), "check");
     const CheckPartial& s = h->hstatus->sum;
     tvcut_stats& st = h->last;
     memset(&st, 0, sizeof(st));
+    bool exact = h->int_w;
+    for (int k = 0; k < h->ndim; ++k) exact = exact && h->int_a[k];
     st.iters = h->iters;
     st.energy = s.energy;
     st.energy_i64 = s.energy_i;
-    bool exact = h->int_w;
-    for (int k = 0; k < h->ndim; ++k) exact = exact && h->int_a[k];
+    st.n_label1 = s.n1;
+    st.threshold = h->p.threshold;
+    // keep the lowest-energy level set (ties: the plain threshold)
+    int best = 0;
+    const LevelPartial& lp = h->hstatus->levels;
+    for (int j = 1; j < L; ++j) {
+        const bool lower = exact ? lp.energy_i[j] < lp.energy_i[best] : lp.energy[j] < lp.energy[best];
+        if (lower) best = j;
+    }
+    if (best > 0) {
+        st.energy = lp.energy[best];
+        st.energy_i64 = lp.energy_i[best];
+        st.n_label1 = lp.n1[best];
+        st.threshold = lv[best];
+        CK(h, traced(h, TVCUT_K_CHECK, 1, [&] { return launch_labels<T>(X_of<T>(h), (T)lv[best], h->labels, h->n, h->stream); }),
+           "check");
+    }
     st.energy_exact = exact ? 1 : 0;
     st.discrete_lb = s.lb;
     st.tv_value = s.tv;
     st.tv_gap = s.tv - s.ytx;
     st.x_absmax = s.xabs;
-    st.n_label1 = s.n1;
-    st.certified = (exact && (double)s.energy_i - s.lb < 1.0) ? 1 : 0;
+    st.certified = (exact && (double)st.energy_i64 - s.lb < 1.0) ? 1 : 0;
     h->labels_valid = true;
     return TVCUT_OK;
 }
@@ -394,6 +435,12 @@ static tvcut_status set_unary_impl(tvcut_t h, const void* w, int dtype, int spac
     if (st != TVCUT_OK) { h->have_w = false; return st; }
     h->have_w = true;
     h->int_w = dtype == TVCUT_I32;
+    {
+        float m;
+        const unsigned bits = h->hstatus->absmax_bits;
+        memcpy(&m, &bits, sizeof(m));
+        h->wmax = (double)m;
+    }
     return cold_start<T>(h);
 }
 
@@ -562,6 +609,7 @@ static tvcut_status project_impl(int ndim, const int64_t* dims, int axis, const 
     A.v = (const T*)v;
     A.a = (const T*)a;
     A.out = (T*)out;
+    A.mapping = -1;
     cudaError_t e = launch_sweep<T>(what == 1 ? MODE_PROX : MODE_PROJ, A, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "tvcut_project_chains");
     return TVCUT_OK;

@@ -46,6 +46,8 @@ struct SweepArgs {
     T* x;              // primal output (LAST modes when check != 0)
     int r;             // number of blocks
     int check;         // LAST modes: also write x
+    int mapping;       // -1 auto, 0 thread per chain from global memory,
+                       // 1/2/3 shared-memory tiles of 8/16/32 chains
 };
 
 // FP64/int64 partial sums of one check (energy, bounds, gaps).
@@ -60,10 +62,20 @@ struct CheckPartial {
     long long pad;
 };
 
+constexpr int kMaxLevels = 17;     // threshold, plus up to 8 levels on each side
+
+struct LevelPartial {
+    double energy[kMaxLevels];
+    long long energy_i[kMaxLevels];
+    long long n1[kMaxLevels];
+};
+
 struct DevStatus {
     CheckPartial sum;
+    LevelPartial levels;
     int flags;          // validation flags of the last conversion
-    int pad[15];
+    unsigned absmax_bits; // max |v| of the last conversion (float bits)
+    int pad[14];
 };
 
 template <typename T>
@@ -78,6 +90,9 @@ struct CheckArgs {
     uint8_t* labels;
     T threshold;
     CheckPartial* partials;
+    int nlevels;                   // level-set ladder size (0: none)
+    T levels[kMaxLevels];
+    LevelPartial* level_partials;
 };
 
 // Validation flags raised by the conversion kernels.
@@ -98,7 +113,9 @@ template <typename T>
 cudaError_t launch_check(const CheckArgs<T>& args, DevStatus* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_convert(const void* src, int src_dtype, T* dst, int64_t n, bool nonneg,
-                           int* flags, cudaStream_t s);
+                           int* flags, unsigned* absmax_bits, cudaStream_t s);
+template <typename T>
+cudaError_t launch_labels(const T* x, T threshold, uint8_t* labels, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_convert_out(const T* src, void* dst, int dst_dtype, int64_t n, cudaStream_t s);
 template <typename T>

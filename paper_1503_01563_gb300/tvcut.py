@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
         ("mapping", ctypes.c_int),
         ("gap_tol", ctypes.c_double),
         ("threshold", ctypes.c_double),
-        ("reserved", ctypes.c_int * 8),
+        ("level_sets", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
     ]
 
 
@@ -56,7 +57,8 @@ class Stats(ctypes.Structure):
         ("tv_gap", ctypes.c_double),
         ("x_absmax", ctypes.c_double),
         ("n_label1", ctypes.c_int64),
-        ("reserved", ctypes.c_int64 * 4),
+        ("threshold", ctypes.c_double),
+        ("reserved", ctypes.c_int64 * 3),
     ]
 
     def as_dict(self):
@@ -253,8 +255,11 @@ class Solver:
     ``iterate(k)``; ``cut()``."""
 
     def __init__(self, dims, algo=AAR, dtype=F32, check_every=10, gap_tol=0.0, threshold=0.0,
-                 stream=None):
+                 stream=None, level_sets=None, mapping=-1):
         p = tvcut_default_params()
+        p.mapping = mapping
+        if level_sets is not None:
+            p.level_sets = level_sets
         p.algo = algo
         p.iterate_dtype = dtype
         p.check_every = check_every

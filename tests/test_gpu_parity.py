@@ -99,10 +99,11 @@ ITER_CASES = [(64, 64), (37, 53), (1, 9), (9, 1), (2, 2), (13, 17, 19), (1, 5, 6
 
 @pytest.mark.parametrize("dims", ITER_CASES)
 @pytest.mark.parametrize("algo", [0, 1])
-def test_iterations_f64(tv, orc, dims, algo):
+@pytest.mark.parametrize("mapping", [-1, 0, 1, 3])
+def test_iterations_f64(tv, orc, dims, algo, mapping):
     w, a = inputs.uniform_grid(dims, 11)
     k = 17
-    s = tv.Solver(dims, algo=algo, dtype=tv.F64, check_every=1000)
+    s = tv.Solver(dims, algo=algo, dtype=tv.F64, check_every=1000, mapping=mapping)
     s.set_problem(w, a)
     s.iterate(k)
     ref_s, ref_x = orc.iterate(algo, w, a, orc.cold_state(algo, w), k)
@@ -132,7 +133,7 @@ def test_check_statistics(tv, orc):
     """Energy, bounds and gaps of a check equal the oracle's on the same x."""
     dims = (31, 29)
     w, a = inputs.uniform_grid(dims, 5)
-    s = tv.Solver(dims, dtype=tv.F64, check_every=1)
+    s = tv.Solver(dims, dtype=tv.F64, check_every=1, level_sets=0)
     s.set_problem(w, a)
     for k in (1, 7, 40):
         _, st = s.iterate(k)
@@ -182,6 +183,28 @@ def test_exact_cut_bruteforce(tv, orc, dims):
             _, st = s.cut()
             assert st.energy_i64 == e, (seed, dt)
             s.close()
+
+
+def test_level_set_ladder(tv, orc):
+    """With level sets on, the check reports the lowest energy among the
+    levels threshold +- S 10^-j (S = max|w|), its labels are x > that level,
+    and that energy is the oracle's energy of those labels."""
+    dims = (40, 36)
+    w, a = inputs.uniform_grid(dims, 8)
+    S = float(np.abs(w).max())
+    s = tv.Solver(dims, dtype=tv.F64, check_every=1, level_sets=8)
+    s.set_problem(w, a)
+    for k in (3, 30):
+        _, st = s.iterate(k)
+        lab, _ = s.cut()
+        x = s.primal()
+        levels = [0.0] + [sg * S * 10.0 ** -(j + 2) for j in range(8) for sg in (1, -1)]
+        energies = [orc.energy(w, a, (x > t).astype(np.uint8)) for t in levels]
+        assert st.energy_i64 == min(energies)
+        assert st.threshold in levels
+        assert np.array_equal(lab, (x > st.threshold).astype(np.uint8))
+        assert orc.energy(w, a, lab) == st.energy_i64
+        assert st.n_label1 == int(lab.sum())
 
 
 def test_exact_cut_3d(tv, orc):
@@ -283,7 +306,8 @@ def test_full_size_3d_volume(tv, orc):
     s.iterate(2)
     _, x = orc.iterate(0, w, a, orc.cold_state(0, w), 2, nthreads=NPROC)
     assert rel_err(s.primal(), x) < 1e-4
-    _, st = s.cut(labels=False)
-    lab = (s.primal() > 0).astype(np.uint8)
+    lab, st = s.cut()
+    x = s.primal(dtype=np.float32)
+    assert np.array_equal(lab, (x > np.float32(st.threshold)).astype(np.uint8))
     assert st.energy_i64 == int(orc.energy(w, a, lab))
     s.close()
