@@ -209,6 +209,32 @@ tvcut_status tvcut_profile(tvcut_t h, int enable);
  * tvcut_profile call; counted always).  Synchronises h's stream. */
 tvcut_status tvcut_profile_read(tvcut_t h, double* ms, int64_t* launches);
 
+/* Iterations without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- code whose framework allocator owns all of the GPU's
+ * memory, or latency-critical loops where a cudaMalloc (which can
+ * synchronise the device) is not acceptable.  It runs `iters` iterations of
+ * `algo` (TVCUT_AAR or TVCUT_AP) exactly like tvcut_iterate, on caller-owned
+ * DEVICE buffers of element type `dtype` (TVCUT_F32 or TVCUT_F64):
+ *   w      n unary values;
+ *   a      a[k] = axis k's compact edge weights (k < ndim);
+ *   state  ndim*n product-space state (z for AAR, lambda for AP), updated in
+ *          place -- start from zeros (AAR) or w/ndim in every block (AP);
+ *   x      NULL, or n values that receive the primal of the last iteration.
+ * The one scratch array an iteration needs (a per-vertex running sum) is a
+ * fixed 8 MiB array inside the library image, so grids are limited to
+ * 2^21 vertices with TVCUT_F32 and 2^20 with TVCUT_F64; larger grids return
+ * TVCUT_ERR_INVALID with a message.  Every GPU that loads the library holds
+ * those 8 MiB until the process exits.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race on it.
+ * Work is ordered on cuda_stream; the call does not synchronise.  Errors
+ * (read with tvcut_last_error(NULL)): INVALID, CUDA. */
+tvcut_status tvcut_iterate_noalloc(int ndim, const int64_t* dims, int algo, int dtype,
+                                   const void* w, const void* const* a, void* state,
+                                   void* x, int64_t iters, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

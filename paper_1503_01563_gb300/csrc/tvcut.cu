@@ -57,6 +57,11 @@ struct tvcut_ctx {
 
 static thread_local std::string g_err;
 
+namespace tvcut {
+// Record a failure of a call without a handle (read by tvcut_last_error(NULL)).
+void set_thread_error(const std::string& msg) { g_err = msg; }
+}  // namespace tvcut
+
 static tvcut_status fail(tvcut_t h, tvcut_status st, const std::string& msg)
 {
     if (h) h->err = msg;

@@ -27,7 +27,7 @@ EXPORTED = [
     "tvcut_default_params", "tvcut_create", "tvcut_destroy", "tvcut_last_error",
     "tvcut_set_unary", "tvcut_set_weights", "tvcut_reset", "tvcut_iterate", "tvcut_cut",
     "tvcut_get_primal", "tvcut_get_state", "tvcut_set_state", "tvcut_warmstart_primal",
-    "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read",
+    "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc",
 ]
 K_SWEEP_FIRST, K_SWEEP_MID, K_SWEEP_LAST, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4, 5
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "tvcut_project_chains": (st, [c_int, P, c_int, P, P, P, c_int, c_int, P]),
         "tvcut_profile": (st, [P, c_int]),
         "tvcut_profile_read": (st, [P, P, P]),
+        "tvcut_iterate_noalloc": (st, [c_int, P, c_int, c_int, P, P, P, P, i64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -248,6 +249,22 @@ def tvcut_profile_read(h):
     n = np.zeros(NKINDS, dtype=np.int64)
     _check(lib().tvcut_profile_read(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(n.ctypes.data)), h)
     return ms, n
+
+
+def tvcut_iterate_noalloc(dims, algo, w, a, state, x=None, iters=1, stream=None):
+    """Iterations on caller-owned device tensors, with no device allocation
+    inside the library (see include/tvcut.h).  w, a[k], state, x: CUDA
+    tensors of one float dtype; state has shape (ndim,) + dims."""
+    dims_arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    pw, sw, dt, _ = _buf(w)
+    bufs = [_buf(ak) for ak in a]
+    ps, ss, dts, _ = _buf(state)
+    px = _buf(x)[0] if x is not None else None
+    if sw != DEVICE or ss != DEVICE or any(b[1] != DEVICE for b in bufs):
+        raise ValueError("tvcut_iterate_noalloc takes device tensors")
+    arr = (ctypes.c_void_p * len(bufs))(*[b[0].value for b in bufs])
+    s = ctypes.c_void_p(int(stream) if stream else 0)
+    return _check(lib().tvcut_iterate_noalloc(len(dims), dims_arr, int(algo), dt, pw, arr, ps, px, int(iters), s))
 
 
 class Solver:
