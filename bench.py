@@ -46,15 +46,14 @@ def make_problem(name):
     return inputs.segmentation_problem(wl["dims"], wl["seed"])
 
 
-def sweep_bytes_per_vertex(ndim):
-    """Algorithmic bytes per vertex of each sweep kind (FP32 state and weights):
-    first: read z_0, w, a_0; write P, y_0.  middle: read z_k, a_k, P; write P,
-    y_k.  last: read z_last, a_last, P, y_0..y_{r-2}; write every z_k.  A check
-    iteration's last sweep also reads w and writes x (+8 B)."""
-    first = 5 * 4
-    mid = 5 * 4
-    last = (3 + (ndim - 1)) * 4 + ndim * 4
-    return first, mid, last
+def kernel_bytes_per_vertex(ndim):
+    """Algorithmic bytes per vertex of one launch of each kernel kind (FP32
+    state and weights; compact weights have dims[k]-1 entries per chain,
+    counted as one per vertex).  prox (the scan launch, all blocks): read s_k
+    and a_k, write x_k, for every block.  update: read w, every s_k and x_k,
+    write every s_k.  A check iteration's update also writes the primal (+4 B).
+    """
+    return {"prox": 12 * ndim, "update": 4 + 12 * ndim}
 
 
 def peaks():
@@ -65,16 +64,16 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def sweep_traffic(kind_name, workload):
-    """DRAM bytes per launch of a sweep kernel from a committed ncu summary,
-    valid only while the kernel sources are unchanged."""
-    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+def kernel_traffic(kind_name, workload):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, valid
+    only while the iteration kernels' source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = hashlib.sha256(open(os.path.join(ROOT, "paper_1503_01563_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
+    src = hashlib.sha256(open(os.path.join(ROOT, "paper_1503_01563_gb300", "csrc", "scan.cu"), "rb").read()).hexdigest()
     ent = d.get(workload, {}).get(kind_name)
-    if not ent or d.get("sweep_cu_sha256") != src:
+    if ent is None or d.get("scan_cu_sha256") != src:
         return None
     return ent
 
@@ -266,25 +265,25 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * n * iters * args.steps / (total_ms / 1e3) / 1e6
 
-    # roofline of the dominant kernel (largest device-time share among sweeps)
-    kinds = ["sweep_first", "sweep_mid", "sweep_last", "check", "other"]
-    bpv = dict(zip(kinds[:3], sweep_bytes_per_vertex(ndim)))
-    dom = max(range(3), key=lambda k: kms[k])
+    # roofline of the dominant kernel (largest device-time share)
+    kinds = ["prox", "update", "check", "other"]
+    bpv = kernel_bytes_per_vertex(ndim)
+    dom = max(range(2), key=lambda k: kms[k])
     dom_name = kinds[dom]
     launches = int(klaunch[dom])
     alg_bytes = bpv[dom_name] * n
-    if dom_name == "sweep_last":
-        alg_bytes += 8 * n * args.steps / max(launches, 1)      # one checked iteration per step
+    if dom_name == "update":
+        alg_bytes += 4 * n * args.steps / max(launches, 1)      # one checked iteration per step
     avg_s = kms[dom] / 1e3 / max(launches, 1)
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_kind = peaks()
-    traffic = sweep_traffic(dom_name, args.workload)
+    traffic = kernel_traffic(dom_name, args.workload)
+    iter_bytes = (bpv["prox"] + bpv["update"]) * n
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
                 "share_of_step": float(kms[dom] / max(kms.sum(), 1e-9)),
-                "all_sweeps_GBps": float(sum(bpv[kinds[k]] * n * klaunch[k] for k in range(3)) /
-                                         max(sum(kms[:3]) / 1e3, 1e-12) / 1e9)}
+                "iteration_GBps": float(iter_bytes * klaunch[0] / max((kms[0] + kms[1]) / 1e3, 1e-12) / 1e9)}
 
     # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
     e2e_solver = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)

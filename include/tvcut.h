@@ -73,10 +73,15 @@ typedef struct {
     int check_every;     /* evaluate labels, energy and gaps every k
                             iterations (default 10; the last iteration of each
                             tvcut_iterate call is always evaluated) */
-    int mapping;         /* chain-to-thread mapping of the sweeps: -1 automatic
-                            (default); 0 one thread per chain reading global
-                            memory; 1, 2, 3 shared-memory tiles of 8, 16, 32
-                            chains (falls back to 0 when a tile does not fit) */
+    int mapping;         /* iteration schedule: -1 automatic (default) or 0:
+                            one scan launch computes the chain prox of every
+                            block (one thread per chain, the last axis' block
+                            stored transposed so that all loads coalesce), then
+                            one elementwise update launch; 1, 2, 3: one fused
+                            sweep per block (prox and update in the same pass)
+                            on shared-memory tiles of 8, 16, 32 chains; 4: the
+                            fused sweeps with one thread per chain reading
+                            global memory */
     double gap_tol;      /* stop when the TV duality gap f(x) - y^T x
                             (Sec. 2.3) is <= gap_tol; 0 disables (default) */
     double threshold;    /* labels are [x_i > threshold] (default 0) */
@@ -191,12 +196,13 @@ tvcut_status tvcut_project_chains(int ndim, const int64_t* dims, int axis,
 
 /* Tracing.  Kernel kinds counted and timed per handle. */
 enum {
-    TVCUT_K_SWEEP_FIRST = 0,   /* chain sweep of block 0 (projection + running sum) */
-    TVCUT_K_SWEEP_MID = 1,     /* chain sweep of a middle block (3D only) */
-    TVCUT_K_SWEEP_LAST = 2,    /* last chain sweep with the fused reflection/averaging update */
-    TVCUT_K_CHECK = 3,         /* threshold + energy + gap evaluation and its reduction */
-    TVCUT_K_OTHER = 4,         /* conversions, cold/warm starts */
-    TVCUT_NKINDS = 5
+    TVCUT_K_PROX = 0,     /* chain prox of the blocks: the scan launch (all blocks
+                             at once), or the fused sweeps of blocks 0..ndim-2 */
+    TVCUT_K_UPDATE = 1,   /* reflection/averaging update: the update launch, or
+                             the fused sweep of the last block */
+    TVCUT_K_CHECK = 2,    /* threshold + energy + gap evaluation and reductions */
+    TVCUT_K_OTHER = 3,    /* conversions, layout changes, cold/warm starts */
+    TVCUT_NKINDS = 4
 };
 
 /* enable != 0: bracket every later kernel launch of h with CUDA events on

@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
             const int64_t j = (g - o * mk * inner) / inner;
             if (j + 1 < mk) {
                 const T x2 = A.x[g + inner];
-                const double ae = (double)A.a[k][g - o * inner];
+                // compact index; the last axis' weights may be stored transposed
+                const int64_t ai = (A.last_transposed && k == A.ndim - 1) ? j * (A.n / mk) + o : g - o * inner;
+                const double ae = (double)A.a[k][ai];
                 acc.tv += ae * fabs(xd - (double)x2);
                 if (l != (x2 > thr)) {
                     acc.energy += ae;
@@ -129,7 +131,8 @@ __global__ void __launch_bounds__(kCheckThreads) level_kernel(CheckArgs<T> A)
             const int64_t jj = (g - o * mk * inner) / inner;
             if (jj + 1 < mk) {
                 const T x2 = A.x[g + inner];
-                const double ae = (double)A.a[k][g - o * inner];
+                const int64_t ai = (A.last_transposed && k == A.ndim - 1) ? jj * (A.n / mk) + o : g - o * inner;
+                const double ae = (double)A.a[k][ai];
                 const long long aei = llrint(ae);
 #pragma unroll
                 for (int j = 0; j < kMaxLevels; ++j)

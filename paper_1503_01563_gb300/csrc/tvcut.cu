@@ -33,6 +33,8 @@ struct tvcut_ctx {
     void* a[3] = {nullptr, nullptr, nullptr};
     int64_t a_len[3] = {0, 0, 0};
     void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
+    void* xk = nullptr;            // ndim * n: per-block prox outputs of the scan schedule
+    bool tlast = true;             // scan schedule: block ndim-1 (state, weights) stored transposed
     uint8_t* labels = nullptr;     // n
     CheckPartial* partials = nullptr;
     LevelPartial* level_partials = nullptr;
@@ -48,8 +50,8 @@ struct tvcut_ctx {
     // tracing: launch counts per kernel kind, and (when enabled) device time
     // from CUDA events recorded around each launch on the handle's stream
     bool prof = false;
-    double prof_ms[TVCUT_NKINDS] = {0, 0, 0, 0, 0};
-    int64_t launches[TVCUT_NKINDS] = {0, 0, 0, 0, 0};
+    double prof_ms[TVCUT_NKINDS] = {0, 0, 0, 0};
+    int64_t launches[TVCUT_NKINDS] = {0, 0, 0, 0};
     struct Pending { int kind; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_pool;
@@ -106,6 +108,7 @@ extern "C" void tvcut_destroy(tvcut_t h)
     cudaFree(h->w);
     for (int k = 0; k < 3; ++k) cudaFree(h->a[k]);
     cudaFree(h->scratch);
+    cudaFree(h->xk);
     cudaFree(h->labels);
     cudaFree(h->partials);
     cudaFree(h->level_partials);
@@ -121,7 +124,7 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP) { why = "params.algo must be TVCUT_AAR or TVCUT_AP"; return false; }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
-    if (p->mapping < -1 || p->mapping > 3) { why = "params.mapping must be -1 (auto) or 0..3"; return false; }
+    if (p->mapping < -1 || p->mapping > 4) { why = "params.mapping must be -1 (auto) or 0..4"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
@@ -156,6 +159,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     h->p = prm;
     h->stream = (cudaStream_t)cuda_stream;
     h->esize = prm.iterate_dtype == TVCUT_F64 ? 8 : 4;
+    h->tlast = prm.mapping <= 0;
     memset(&h->last, 0, sizeof(h->last));
     const size_t es = (size_t)h->esize;
     cudaError_t e = cudaSuccess;
@@ -166,6 +170,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
         e = cudaMalloc(&h->a[k], es * (size_t)(h->a_len[k] > 0 ? h->a_len[k] : 1));
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
+    if (e == cudaSuccess) e = cudaMalloc(&h->xk, es * (size_t)(ndim * n));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->labels, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(CheckPartial) * kCheckBlocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->level_partials, sizeof(LevelPartial) * kCheckBlocks);
@@ -188,6 +193,23 @@ template <typename T>
 static T* X_of(tvcut_t h) { return (T*)h->scratch + h->n; }
 template <typename T>
 static T* S_of(tvcut_t h, int k) { return (T*)h->state + (int64_t)k * h->n; }
+template <typename T>
+static T* XK_of(tvcut_t h, int k) { return (T*)h->xk + (int64_t)k * h->n; }
+static int64_t cols_of(tvcut_t h) { return h->dims[h->ndim - 1]; }
+static int64_t rows_of(tvcut_t h) { return h->n / h->dims[h->ndim - 1]; }
+
+// In-place layout change of an (rows x cols) array through the xk area
+// (free outside iterations): natural -> transposed (forward) or back.
+template <typename T>
+static cudaError_t relayout(tvcut_t h, T* arr, int64_t rows, int64_t cols, bool forward)
+{
+    if (rows * cols <= 0) return cudaSuccess;
+    T* tmp = XK_of<T>(h, 0);
+    cudaError_t e = forward ? launch_transpose<T>(arr, tmp, rows, cols, h->stream)
+                            : launch_transpose<T>(arr, tmp, cols, rows, h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(arr, tmp, sizeof(T) * (size_t)(rows * cols), cudaMemcpyDeviceToDevice, h->stream);
+}
 
 // ---- tracing ----------------------------------------------------------------
 
@@ -277,6 +299,9 @@ static tvcut_status cold_start(tvcut_t h)
     if (h->p.algo == TVCUT_AP) {
         CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_cold_ap<T>((const T*)h->w, (T*)h->state, h->ndim, h->n, h->stream); }),
            "cold start");
+        if (h->tlast)
+            CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true); }),
+               "cold start");
     } else {
         CK(h, cudaMemsetAsync(h->state, 0, (size_t)h->esize * (size_t)(h->ndim * h->n), h->stream), "cold start");
     }
@@ -310,13 +335,55 @@ static cudaError_t run_sweeps(tvcut_t h, int first, int mid, int last, int check
         A.x = X_of<T>(h);
         A.r = r;
         A.check = check;
-        A.mapping = h->p.mapping;
+        A.mapping = h->p.mapping == 4 ? 0 : h->p.mapping;
         const int mode = k == 0 ? first : (k == r - 1 ? last : mid);
-        const int kind = k == 0 ? TVCUT_K_SWEEP_FIRST : (k == r - 1 ? TVCUT_K_SWEEP_LAST : TVCUT_K_SWEEP_MID);
+        const int kind = k == r - 1 ? TVCUT_K_UPDATE : TVCUT_K_PROX;
         cudaError_t e = traced(h, kind, 1, [&] { return launch_sweep<T>(mode, A, h->stream); });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// One iteration (or, with mode UPD_EVAL, only the primal of the current
+// state).  Scan schedule: one scan launch for all blocks + one update launch;
+// fused schedule (mapping 1..4): one sweep per block, the last one updating.
+template <typename T>
+static cudaError_t run_iteration(tvcut_t h, int mode, int check)
+{
+    if (!h->tlast) {
+        if (mode == UPD_EVAL) return run_sweeps<T>(h, MODE_EVAL_FIRST, MODE_EVAL_MID, MODE_EVAL_LAST, 1);
+        if (mode == UPD_AAR) return run_sweeps<T>(h, MODE_AAR_FIRST, MODE_AAR_MID, MODE_AAR_LAST, check);
+        return run_sweeps<T>(h, MODE_AP_FIRST, MODE_AP_MID, MODE_AP_LAST, check);
+    }
+    const int r = h->ndim;
+    ScanArgs<T> S;
+    memset(&S, 0, sizeof(S));
+    S.naxes = r;
+    for (int k = 0; k < r; ++k) {
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        S.ax[k].nchains = g.nchains;
+        S.ax[k].inner = g.inner;
+        S.ax[k].m = g.m;
+        S.ax[k].transposed = k == r - 1 ? 1 : 0;
+        S.ax[k].v = S_of<T>(h, k);
+        S.ax[k].a = (const T*)h->a[k];
+        S.ax[k].x = XK_of<T>(h, k);
+    }
+    cudaError_t e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
+    if (e != cudaSuccess) return e;
+    UpdateArgs<T> U;
+    memset(&U, 0, sizeof(U));
+    U.rows = rows_of(h);
+    U.cols = cols_of(h);
+    U.r = r;
+    U.check = check;
+    for (int k = 0; k < r; ++k) {
+        U.s[k] = S_of<T>(h, k);
+        U.x[k] = XK_of<T>(h, k);
+    }
+    U.w = (const T*)h->w;
+    U.xout = X_of<T>(h);
+    return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_update<T>(mode, U, h->stream); });
 }
 
 template <typename T>
@@ -336,6 +403,7 @@ static tvcut_status run_check(tvcut_t h)
     C.w = (const T*)h->w;
     C.labels = h->labels;
     C.threshold = (T)h->p.threshold;
+    C.last_transposed = h->tlast ? 1 : 0;
     C.partials = h->partials;
     // level-set ladder: threshold, then threshold +- S 10^-j, j = 2, 3, ...
     double lv[kMaxLevels];
@@ -394,7 +462,7 @@ template <typename T>
 static tvcut_status ensure_primal(tvcut_t h)
 {
     if (h->x_valid) return TVCUT_OK;
-    CK(h, run_sweeps<T>(h, MODE_EVAL_FIRST, MODE_EVAL_MID, MODE_EVAL_LAST, 1), "evaluate primal");
+    CK(h, run_iteration<T>(h, UPD_EVAL, 1), "evaluate primal");
     h->x_valid = true;
     h->labels_valid = false;
     return TVCUT_OK;
@@ -403,14 +471,11 @@ static tvcut_status ensure_primal(tvcut_t h)
 template <typename T>
 static tvcut_status iterate_impl(tvcut_t h, int64_t max_iters, tvcut_stats* out)
 {
-    const bool aar = h->p.algo == TVCUT_AAR;
-    const int first = aar ? MODE_AAR_FIRST : MODE_AP_FIRST;
-    const int mid = aar ? MODE_AAR_MID : MODE_AP_MID;
-    const int last = aar ? MODE_AAR_LAST : MODE_AP_LAST;
+    const int mode = h->p.algo == TVCUT_AAR ? UPD_AAR : UPD_AP;
     tvcut_status ret = TVCUT_NOT_CONVERGED;
     for (int64_t it = 0; it < max_iters; ++it) {
         const bool check = ((h->iters + 1) % h->p.check_every == 0) || it == max_iters - 1;
-        CK(h, run_sweeps<T>(h, first, mid, last, check ? 1 : 0), "iterate");
+        CK(h, run_iteration<T>(h, mode, check ? 1 : 0), "iterate");
         h->iters += 1;
         h->x_valid = false;
         h->labels_valid = false;
@@ -460,6 +525,8 @@ static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dty
 {
     tvcut_status st = ingest<T>(h, a, dtype, space, h->a_len[axis], true, (T*)h->a[axis], "tvcut_set_weights");
     if (st != TVCUT_OK) { h->have_a[axis] = false; return st; }
+    if (h->tlast && axis == h->ndim - 1)
+        CK(h, relayout<T>(h, (T*)h->a[axis], rows_of(h), cols_of(h) - 1, true), "tvcut_set_weights");
     h->have_a[axis] = true;
     h->int_a[axis] = dtype == TVCUT_I32;
     if (h->have_w) return cold_start<T>(h);
@@ -551,15 +618,42 @@ extern "C" tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int spac
     return DISPATCH(h, get_primal_impl, h, x, dtype, space);
 }
 
+template <typename T>
+static tvcut_status get_state_impl(tvcut_t h, void* s, int space)
+{
+    const int r = h->ndim;
+    const cudaMemcpyKind kind = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int plain = h->tlast ? r - 1 : r;
+    CK(h, cudaMemcpyAsync(s, h->state, sizeof(T) * (size_t)(plain * h->n), kind, h->stream), "tvcut_get_state");
+    if (h->tlast) {
+        // the last block back to grid layout through the xk area
+        T* tmp = XK_of<T>(h, 0);
+        CK(h, launch_transpose<T>(S_of<T>(h, r - 1), tmp, cols_of(h), rows_of(h), h->stream), "tvcut_get_state");
+        CK(h, cudaMemcpyAsync((T*)s + (int64_t)(r - 1) * h->n, tmp, sizeof(T) * (size_t)h->n, kind, h->stream),
+           "tvcut_get_state");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_state");
+    return TVCUT_OK;
+}
+
 extern "C" tvcut_status tvcut_get_state(tvcut_t h, void* s, int space)
 {
     if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_get_state: NULL handle");
     if (!s) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: NULL output");
     if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: bad space");
-    CK(h, cudaMemcpyAsync(s, h->state, (size_t)h->esize * (size_t)(h->ndim * h->n),
-                          space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
-       "tvcut_get_state");
-    CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_state");
+    return DISPATCH(h, get_state_impl, h, s, space);
+}
+
+template <typename T>
+static tvcut_status set_state_impl(tvcut_t h, const void* s, int space)
+{
+    CK(h, cudaMemcpyAsync(h->state, s, sizeof(T) * (size_t)(h->ndim * h->n),
+                          space == TVCUT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
+       "tvcut_set_state");
+    if (h->tlast)
+        CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_set_state");
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_set_state");
+    h->x_valid = h->labels_valid = false;
     return TVCUT_OK;
 }
 
@@ -568,12 +662,7 @@ extern "C" tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space)
     if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_set_state: NULL handle");
     if (!s) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_state: NULL input");
     if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_state: bad space");
-    CK(h, cudaMemcpyAsync(h->state, s, (size_t)h->esize * (size_t)(h->ndim * h->n),
-                          space == TVCUT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
-       "tvcut_set_state");
-    CK(h, cudaStreamSynchronize(h->stream), "tvcut_set_state");
-    h->x_valid = h->labels_valid = false;
-    return TVCUT_OK;
+    return DISPATCH(h, set_state_impl, h, s, space);
 }
 
 template <typename T>
@@ -588,6 +677,8 @@ static tvcut_status warmstart_impl(tvcut_t h, const float* xhat, float tau, int 
     // the kernel reads xhat[i] before writing state; state and scratch are disjoint
     CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_warmstart<T>((const T*)h->w, d, tau, (T*)h->state, h->ndim, h->n, h->stream); }),
        "tvcut_warmstart_primal");
+    if (h->tlast)
+        CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_warmstart_primal");
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_warmstart_primal");
     h->x_valid = h->labels_valid = false;
     h->iters = 0;

@@ -19,6 +19,44 @@ struct ChainGeom {
     int m;
 };
 
+// One block of the scan launch (scan.cu): every chain of one axis.  Element j
+// of chain c sits at o*m*inner + q + j*inner (c = o*inner + q), or, when
+// `transposed`, at j*nchains + c; the weights follow the same rule with m-1
+// elements per chain.
+template <typename T>
+struct ScanAxis {
+    int64_t nchains;
+    int64_t inner;
+    int64_t block_begin;   // first CTA of this axis (set by the launcher)
+    int m;
+    int transposed;
+    const T* v;
+    const T* a;
+    T* x;
+};
+
+template <typename T>
+struct ScanArgs {
+    int naxes;
+    ScanAxis<T> ax[3];
+};
+
+enum UpdateMode : int { UPD_AAR = 0, UPD_AP = 1, UPD_EVAL = 2 };
+
+// Elementwise update over the grid viewed as rows x cols (cols = last dim);
+// block r-1 (s and x) is stored transposed.
+template <typename T>
+struct UpdateArgs {
+    int64_t rows;
+    int64_t cols;
+    int r;
+    int check;
+    T* s[3];
+    const T* x[3];
+    const T* w;
+    T* xout;
+};
+
 // Per-element epilogues of one chain sweep (what is done with y = v - prox(v)).
 enum SweepMode : int {
     MODE_PROJ = 0,      // out = y
@@ -89,6 +127,7 @@ struct CheckArgs {
     const T* a[3];
     uint8_t* labels;
     T threshold;
+    int last_transposed;           // weights of axis ndim-1 stored transposed
     CheckPartial* partials;
     int nlevels;                   // level-set ladder size (0: none)
     T levels[kMaxLevels];
@@ -123,6 +162,14 @@ cudaError_t launch_cold_ap(const T* w, T* state, int r, int64_t n, cudaStream_t 
 template <typename T>
 cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state, int r,
                              int64_t n, cudaStream_t s);
+
+// Launchers (scan.cu)
+template <typename T>
+cudaError_t launch_scan(ScanArgs<T> args, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update(int mode, const UpdateArgs<T>& args, cudaStream_t s);
+template <typename T>
+cudaError_t launch_transpose(const T* in, T* out, int64_t rows, int64_t cols, cudaStream_t s);
 
 ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
 

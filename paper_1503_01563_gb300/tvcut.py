@@ -29,7 +29,7 @@ EXPORTED = [
     "tvcut_get_primal", "tvcut_get_state", "tvcut_set_state", "tvcut_warmstart_primal",
     "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc",
 ]
-K_SWEEP_FIRST, K_SWEEP_MID, K_SWEEP_LAST, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4, 5
+K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
 
 class Params(ctypes.Structure):
