@@ -11,7 +11,7 @@
 //           ("chain-major"): the natural row-major layout already is for
 //           every axis but the last, and the last axis' block (rows) is kept
 //           transposed.  A warp's loads of one step are thus one 128-byte
-//           line; lines further down the chain are prefetched into L1.
+//           line.
 //
 //   update: per vertex, y_k = s_k - x_k and
 //             AAR (Eq. 3 with Eq. dualA): s_k <- y_k + (w - 2 sum y + sum s)/r
@@ -24,12 +24,6 @@
 namespace tvcut {
 
 constexpr int kScanThreads = 128;
-constexpr int kPrefetch = 12;        // elements ahead prefetched into L1
-
-__device__ __forceinline__ void prefetch_l1(const void* p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 // Taut-string scan of one chain: element j of v at v[j*stride], weight of
 // edge (j, j+1) at a[j*stride]; writes x[j*stride] = prox value.  From a
@@ -38,55 +32,56 @@ __device__ __forceinline__ void prefetch_l1(const void* p)
 // at the chain end).  th/tl are the largest/smallest feasible t and uh/ul the
 // matching u_i; when the feasible set empties, the segment ends at the point
 // that last limited the violated bound (the string bends there) and the scan
-// resumes after it.
+// resumes after it.  Pointers advance by `stride` per element; only a rescan
+// recomputes them.
+template <typename T>
+__device__ __forceinline__ T div_len(T num, int len)
+{
+    if constexpr (sizeof(T) == 4) return num * __frcp_rn((float)len);   // 1/len correctly rounded
+    else return num / (T)len;
+}
+
 template <typename T>
 __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const T* __restrict__ a,
                                            T* __restrict__ x, int64_t stride)
 {
-    int s = 0, i = 0, ih = 0, il = 0, ipf = 0;
+    int s = 0, i = 0, ih = 0, il = 0;
     T u0 = T(0), th = T(0), tl = T(0), uh = T(0), ul = T(0), ah = T(0), al = T(0);
-    for (int p = 0; p < kPrefetch && p < m; ++p) {
-        prefetch_l1(v + (int64_t)p * stride);
-        prefetch_l1(a + (int64_t)p * stride);
-    }
-    ipf = kPrefetch;
+    const T* pv = v;
+    const T* pa = a;
+    T* px = x;                                   // next element to write
     for (;;) {
-        if (i + kPrefetch >= ipf && ipf < m) {
-            prefetch_l1(v + (int64_t)ipf * stride);
-            prefetch_l1(a + (int64_t)ipf * stride);
-            ++ipf;
-        }
-        const T vi = v[(int64_t)i * stride];
-        const T Ai = (i < m - 1) ? a[(int64_t)i * stride] : T(0);
+        const T vi = *pv;
+        const T Ai = (i < m - 1) ? *pa : T(0);
         bool init = (i == s);
         if (!init) {
             uh += th - vi;
             ul += tl - vi;
-            int e = -1;
-            T t = T(0);
-            if (uh < -Ai) {            // bend up at ih
-                e = ih; t = th; u0 = ah;
-            } else if (ul > Ai) {      // bend down at il
-                e = il; t = tl; u0 = -al;
-            }
-            if (e >= 0) {
-                for (int j = s; j <= e; ++j) x[(int64_t)j * stride] = t;
+            const bool bhi = uh < -Ai;
+            const bool blo = !bhi && ul > Ai;
+            if (bhi || blo) {                        // the string bends at e
+                const int e = bhi ? ih : il;
+                const T t = bhi ? th : tl;
+                u0 = bhi ? ah : -al;
+                for (int j = s; j <= e; ++j, px += stride) *px = t;
                 s = e + 1;
-                if (s < i) {           // rescan from the bend
+                if (s < i) {                         // rescan from the bend
                     i = s;
+                    pv = v + (int64_t)s * stride;
+                    pa = a + (int64_t)s * stride;
                     continue;
                 }
-                init = true;           // the new segment starts at i
+                init = true;                         // the new segment starts at i
             } else {
-                const T len = T(i - s + 1);
+                const int len = i - s + 1;
                 if (uh > Ai) {
-                    th -= (uh - Ai) / len;
+                    th -= div_len<T>(uh - Ai, len);
                     uh = Ai;
                     ih = i;
                     ah = Ai;
                 }
                 if (ul < -Ai) {
-                    tl += (-Ai - ul) / len;
+                    tl += div_len<T>(-Ai - ul, len);
                     ul = -Ai;
                     il = i;
                     al = Ai;
@@ -102,10 +97,12 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
             ah = al = Ai;
         }
         if (i == m - 1) {
-            for (int j = s; j <= m - 1; ++j) x[(int64_t)j * stride] = th;
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
             break;
         }
         ++i;
+        pv += stride;
+        pa += stride;
     }
 }
 
