@@ -54,46 +54,124 @@ __device__ CheckPartial block_reduce(CheckPartial p)
     return p;
 }
 
-template <typename T>
+// One pass over the grid: labels at the plain threshold, the FP64 sums of the
+// check (discrete lower bound, y^T x, f(x), max |x|) and the energies of the
+// level sets [x > levels[j]] (Sec. 2.1: every level set of a solution of the
+// relaxation solves (D)); level 0 is the plain threshold.  Each warp walks
+// whole rows of the last axis, so a vertex's neighbours along every axis are
+// at fixed offsets (+1, +W, +H*W) and the row's coordinates come from one
+// division per row.  A vertex's level labels form a bit mask; an edge adds
+// its weight to the levels whose bit differs at its two ends.  Integer
+// problems accumulate level energies in exact int64, others in FP64.
+template <typename T, bool EXACT>
 __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
 {
+    using Acc = typename std::conditional<EXACT, long long, double>::type;
     CheckPartial acc{0, 0, 0, 0, 0, 0, 0, 0};
+    Acc el[kMaxLevels];
+    int n1l[kMaxLevels];
+#pragma unroll
+    for (int j = 0; j < kMaxLevels; ++j) { el[j] = 0; n1l[j] = 0; }
+    const int L = A.nlevels;
+    const int nd = A.ndim;
+    const int64_t W = A.dims[nd - 1];
+    const int64_t R = A.n / W;
+    const int64_t Hm = nd >= 2 ? A.dims[nd - 2] : 1;          // axis nd-2 extent
+    const int64_t D0 = nd == 3 ? A.dims[0] : 1;
     const T thr = A.threshold;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n; g += stride) {
-        const T xg = A.x[g];
-        const bool l = xg > thr;
-        A.labels[g] = (uint8_t)l;
-        const double wg = (double)A.w[g];
-        const double xd = (double)xg;
-        acc.lb -= fmax(xd, 0.0);
-        acc.ytx += (wg - xd) * xd;
-        acc.xabs = fmax(acc.xabs, fabs(xd));
-        if (l) {
-            acc.energy -= wg;
-            acc.energy_i -= llrint(wg);
-            acc.n1 += 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kCheckThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kCheckThreads) >> 5;
+    auto mask_of = [&](T xv) {
+        unsigned mk = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxLevels; ++j)
+            if (j < L && xv > A.levels[j]) mk |= 1u << j;
+        return mk;
+    };
+    auto add_edge = [&](double xd, T x2, unsigned mk, bool l, double ae) {
+        acc.tv += ae * fabs(xd - (double)x2);
+        if (l != (x2 > thr)) {
+            acc.energy += ae;
+            acc.energy_i += llrint(ae);
         }
-        for (int k = 0; k < A.ndim; ++k) {
-            const int64_t inner = A.inner[k];
-            const int64_t mk = A.dims[k];
-            const int64_t o = g / (mk * inner);
-            const int64_t j = (g - o * mk * inner) / inner;
-            if (j + 1 < mk) {
-                const T x2 = A.x[g + inner];
-                // compact index; the last axis' weights may be stored transposed
-                const int64_t ai = (A.last_transposed && k == A.ndim - 1) ? j * (A.n / mk) + o : g - o * inner;
-                const double ae = (double)A.a[k][ai];
-                acc.tv += ae * fabs(xd - (double)x2);
-                if (l != (x2 > thr)) {
-                    acc.energy += ae;
-                    acc.energy_i += llrint(ae);
-                }
+        const unsigned diff = mk ^ mask_of(x2);
+        const Acc av = EXACT ? (Acc)llrint(ae) : (Acc)ae;
+#pragma unroll
+        for (int j = 0; j < kMaxLevels; ++j)
+            if ((diff >> j) & 1u) el[j] += av;
+    };
+    for (int64_t r = warp; r < R; r += nwarps) {
+        const int64_t h = r % Hm;                 // coordinate along axis nd-2
+        const int64_t d = r / Hm;                 // coordinate along axis 0 (3D)
+        for (int64_t c = lane; c < W; c += 32) {
+            const int64_t g = r * W + c;
+            const T xg = A.x[g];
+            const bool l = xg > thr;
+            A.labels[g] = (uint8_t)l;
+            const double wg = (double)A.w[g];
+            const double xd = (double)xg;
+            acc.lb -= fmax(xd, 0.0);
+            acc.ytx += (wg - xd) * xd;
+            acc.xabs = fmax(acc.xabs, fabs(xd));
+            if (l) {
+                acc.energy -= wg;
+                acc.energy_i -= llrint(wg);
+                acc.n1 += 1;
             }
+            const unsigned mk = mask_of(xg);
+            const Acc wv = EXACT ? (Acc)llrint(wg) : (Acc)wg;
+#pragma unroll
+            for (int j = 0; j < kMaxLevels; ++j)
+                if ((mk >> j) & 1u) { el[j] -= wv; n1l[j] += 1; }
+            // last axis: edge (c, c+1) of row r
+            if (c + 1 < W) {
+                const int64_t ai = A.last_transposed ? c * R + r : r * (W - 1) + c;
+                add_edge(xd, A.x[g + 1], mk, l, (double)A.a[nd - 1][ai]);
+            }
+            // axis nd-2: edge (h, h+1); compact index ((d*(Hm-1) + h) * W + c)
+            if (h + 1 < Hm) add_edge(xd, A.x[g + W], mk, l, (double)A.a[nd - 2][(d * (Hm - 1) + h) * W + c]);
+            // axis 0 of a 3D grid: edge (d, d+1); compact index = g
+            if (nd == 3 && d + 1 < D0) add_edge(xd, A.x[g + Hm * W], mk, l, (double)A.a[0][g]);
         }
     }
-    CheckPartial r = block_reduce<kCheckThreads>(acc);
-    if (threadIdx.x == 0) A.partials[blockIdx.x] = r;
+    CheckPartial rsum = block_reduce<kCheckThreads>(acc);
+    if (threadIdx.x == 0) A.partials[blockIdx.x] = rsum;
+    // level partials, one level at a time in a fixed order
+    __shared__ double se[kCheckThreads / 32];
+    __shared__ long long sei[kCheckThreads / 32];
+    __shared__ long long sn[kCheckThreads / 32];
+    const int wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kMaxLevels; ++j) {
+        if (j >= L) break;
+        Acc a = el[j];
+        long long c = n1l[j];
+        for (int dd = 16; dd > 0; dd >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, dd);
+            c += __shfl_down_sync(0xffffffffu, c, dd);
+        }
+        __syncthreads();
+        if (lane == 0) {
+            if (EXACT) sei[wid] = (long long)a;
+            else se[wid] = (double)a;
+            sn[wid] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0;
+            long long tb = 0, tc = 0;
+            for (int w = 0; w < kCheckThreads / 32; ++w) {
+                if (EXACT) tb += sei[w];
+                else ta += se[w];
+                tc += sn[w];
+            }
+            if (EXACT) ta = (double)tb;
+            A.level_partials[blockIdx.x].energy[j] = ta;
+            A.level_partials[blockIdx.x].energy_i[j] = tb;
+            A.level_partials[blockIdx.x].n1[j] = tc;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) finalize_kernel(const CheckPartial* partials, int count,
@@ -103,71 +181,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const CheckPartial* parti
     for (int i = threadIdx.x; i < count; i += blockDim.x) partial_add(acc, partials[i]);
     CheckPartial r = block_reduce<256>(acc);
     if (threadIdx.x == 0) status->sum = r;
-}
-
-// Energies of the level sets [x > levels[j]] (Sec. 2.1: every level set of a
-// solution of the relaxation solves (D)), FP64 and exact int64.
-template <typename T>
-__global__ void __launch_bounds__(kCheckThreads) level_kernel(CheckArgs<T> A)
-{
-    double e[kMaxLevels];
-    long long ei[kMaxLevels];
-    int n1[kMaxLevels];
-#pragma unroll
-    for (int j = 0; j < kMaxLevels; ++j) { e[j] = 0.0; ei[j] = 0; n1[j] = 0; }
-    const int L = A.nlevels;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n; g += stride) {
-        const T xg = A.x[g];
-        const double wg = (double)A.w[g];
-        const long long wi = llrint(wg);
-#pragma unroll
-        for (int j = 0; j < kMaxLevels; ++j)
-            if (j < L && xg > A.levels[j]) { e[j] -= wg; ei[j] -= wi; n1[j] += 1; }
-        for (int k = 0; k < A.ndim; ++k) {
-            const int64_t inner = A.inner[k];
-            const int64_t mk = A.dims[k];
-            const int64_t o = g / (mk * inner);
-            const int64_t jj = (g - o * mk * inner) / inner;
-            if (jj + 1 < mk) {
-                const T x2 = A.x[g + inner];
-                const int64_t ai = (A.last_transposed && k == A.ndim - 1) ? jj * (A.n / mk) + o : g - o * inner;
-                const double ae = (double)A.a[k][ai];
-                const long long aei = llrint(ae);
-#pragma unroll
-                for (int j = 0; j < kMaxLevels; ++j)
-                    if (j < L && ((xg > A.levels[j]) != (x2 > A.levels[j]))) { e[j] += ae; ei[j] += aei; }
-            }
-        }
-    }
-    // block reduction, one level at a time, fixed order
-    __shared__ double se[kCheckThreads / 32];
-    __shared__ long long sei[kCheckThreads / 32];
-    __shared__ long long sn[kCheckThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < kMaxLevels; ++j) {
-        if (j >= L) break;
-        double a = e[j];
-        long long b = ei[j];
-        long long c = n1[j];
-        for (int d = 16; d > 0; d >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, d);
-            b += __shfl_down_sync(0xffffffffu, b, d);
-            c += __shfl_down_sync(0xffffffffu, c, d);
-        }
-        if (lane == 0) { se[wid] = a; sei[wid] = b; sn[wid] = c; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double ta = 0.0;
-            long long tb = 0, tc = 0;
-            for (int w = 0; w < kCheckThreads / 32; ++w) { ta += se[w]; tb += sei[w]; tc += sn[w]; }
-            A.level_partials[blockIdx.x].energy[j] = ta;
-            A.level_partials[blockIdx.x].energy_i[j] = tb;
-            A.level_partials[blockIdx.x].n1[j] = tc;
-        }
-        __syncthreads();
-    }
 }
 
 __global__ void __launch_bounds__(32) level_finalize_kernel(const LevelPartial* partials, int count, int L,
@@ -188,17 +201,15 @@ __global__ void __launch_bounds__(32) level_finalize_kernel(const LevelPartial* 
 }
 
 template <typename T>
-cudaError_t launch_check(const CheckArgs<T>& A, DevStatus* status, cudaStream_t s)
+cudaError_t launch_check(const CheckArgs<T>& A, bool exact, DevStatus* status, cudaStream_t s)
 {
-    check_kernel<T><<<kCheckBlocks, kCheckThreads, 0, s>>>(A);
+    if (exact) check_kernel<T, true><<<kCheckBlocks, kCheckThreads, 0, s>>>(A);
+    else check_kernel<T, false><<<kCheckBlocks, kCheckThreads, 0, s>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_kernel<<<1, 256, 0, s>>>(A.partials, kCheckBlocks, status);
     e = cudaGetLastError();
     if (e != cudaSuccess || A.nlevels <= 0) return e;
-    level_kernel<T><<<kCheckBlocks, kCheckThreads, 0, s>>>(A);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     level_finalize_kernel<<<1, 32, 0, s>>>(A.level_partials, kCheckBlocks, A.nlevels, status);
     return cudaGetLastError();
 }
@@ -325,7 +336,7 @@ cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state,
 }
 
 #define TVCUT_INST(T)                                                                          \
-    template cudaError_t launch_check<T>(const CheckArgs<T>&, DevStatus*, cudaStream_t);        \
+    template cudaError_t launch_check<T>(const CheckArgs<T>&, bool, DevStatus*, cudaStream_t);  \
     template cudaError_t launch_convert<T>(const void*, int, T*, int64_t, bool, int*, unsigned*, cudaStream_t); \
     template cudaError_t launch_labels<T>(const T*, T, uint8_t*, int64_t, cudaStream_t);         \
     template cudaError_t launch_convert_out<T>(const T*, void*, int, int64_t, cudaStream_t);    \

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(UpdateArgs<T> A)
     const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;    // 32 x 8
 
     // stage the transposed block: element (r0+rr, c0+cc) at (c0+cc)*R + r0+rr
+#pragma unroll
     for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
         const int64_t c = c0 + cc, r = r0 + tx;
         if (c < W && r < R) {
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(UpdateArgs<T> A)
         }
     }
     __syncthreads();
+#pragma unroll
     for (int rr = ty; rr < kTile; rr += kUpdThreads / kTile) {
         const int64_t r = r0 + rr, c = c0 + tx;
         if (r >= R || c >= W) continue;
@@ -203,6 +205,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(UpdateArgs<T> A)
     }
     if constexpr (MODE != UPD_EVAL) {
         __syncthreads();
+#pragma unroll
         for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
             const int64_t c = c0 + cc, r = r0 + tx;
             if (c < W && r < R) A.s[last][c * R + r] = sz[cc][tx];

@@ -419,7 +419,10 @@ static tvcut_status run_check(tvcut_t h)
     C.nlevels = L;
     for (int j = 0; j < L; ++j) C.levels[j] = (T)lv[j];
     C.level_partials = h->level_partials;
-    CK(h, traced(h, TVCUT_K_CHECK, L > 0 ? 4 : 2, [&] { return launch_check<T>(C, h->dstatus, h->stream); }), "check");
+    bool exact_data = h->int_w;
+    for (int k = 0; k < h->ndim; ++k) exact_data = exact_data && h->int_a[k];
+    CK(h, traced(h, TVCUT_K_CHECK, L > 0 ? 3 : 2, [&] { return launch_check<T>(C, exact_data, h->dstatus, h->stream); }),
+       "check");
     CK(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream), "check");
     CK(h, cudaStreamSynchronize(h->stream), "check");
     CK(h, flush_trace(h), "check");

@@ -149,7 +149,7 @@ cudaError_t launch_sweep(int mode, const SweepArgs<T>& args, cudaStream_t s);
 constexpr int kCheckBlocks = 608;     // 4 x 152 SMs
 constexpr int kCheckThreads = 256;
 template <typename T>
-cudaError_t launch_check(const CheckArgs<T>& args, DevStatus* status, cudaStream_t s);
+cudaError_t launch_check(const CheckArgs<T>& args, bool exact, DevStatus* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_convert(const void* src, int src_dtype, T* dst, int64_t n, bool nonneg,
                            int* flags, unsigned* absmax_bits, cudaStream_t s);
