@@ -75,9 +75,13 @@ typedef struct {
                             tvcut_iterate call is always evaluated) */
     int mapping;         /* iteration schedule: -1 automatic (default) or 0:
                             one scan launch computes the chain prox of every
-                            block (one thread per chain, the last axis' block
-                            stored transposed so that all loads coalesce), then
-                            one elementwise update launch; 1, 2, 3: one fused
+                            block (the last axis' block stored transposed so
+                            that all loads coalesce), then one elementwise
+                            update launch; the scan gives each chain a thread,
+                            or, when there are too few chains to fill the GPU,
+                            a warp (speculative pieces, see csrc/scan.cu);
+                            5, 6: that schedule with thread-per-chain or
+                            warp-per-chain scans forced; 1, 2, 3: one fused
                             sweep per block (prox and update in the same pass)
                             on shared-memory tiles of 8, 16, 32 chains; 4: the
                             fused sweeps with one thread per chain reading

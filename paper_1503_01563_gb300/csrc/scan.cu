@@ -25,6 +25,20 @@ namespace tvcut {
 
 constexpr int kScanThreads = 128;
 
+__device__ __forceinline__ void scan_cp_async(void* smem, const void* gmem, int bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+template <typename T>
+__device__ __forceinline__ void scan_cp_elem(T* smem, const T* gmem) { scan_cp_async(smem, gmem, (int)sizeof(T)); }
+__device__ __forceinline__ void scan_cp_wait()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Taut-string scan of one chain: element j of v at v[j*stride], weight of
 // edge (j, j+1) at a[j*stride]; writes x[j*stride] = prox value.  From a
 // segment start s with incoming multiplier u0, a common value t on s..i gives
@@ -129,17 +143,254 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
     scan_chain<T>(X.m, X.v + base, X.a + abase, X.x + base, stride);
 }
 
+// ---- warp-per-chain speculative scan ------------------------------------------
+//
+// For few, long chains (a 2D grid has only H + W of them) one thread per chain
+// leaves the GPU idle, so a warp shares one chain: lane L scans piece L of 32
+// from a guessed state (a segment starts at the piece start with multiplier
+// 0; exact for lane 0) and records every bend it finds (position e and
+// direction).  After a bend at e the scan state is fixed (the next segment
+// starts at e+1 with multiplier +-a_e), so a lane's trajectory is the true one
+// from the first bend it shares with the true scan.  Lane L then continues
+// from its own piece end into piece L+1 until it produces a bend that lane
+// L+1 (or any later lane) recorded; that lane's results after the bend are
+// then exact, and lane L rewrites every position before it.  Lane 0 is
+// exact, so following merges from lane 0 reaches the chain end through
+// verified lanes only; lanes not on that path are overwritten.
+
+template <typename T>
+struct LaneState {
+    int s, i, ih, il;
+    T u0, th, tl, uh, ul, ah, al;
+};
+
+__host__ __device__ __forceinline__ int skew32(int j) { return j + (j >> 5); }
+
+// Advance one lane's scan through positions st.i .. stop-1 (data in shared
+// memory, skewed).  on_bend(s, e, d, t) is called for every finished segment
+// [s, e] with value t (d = 1: the string bends up at e, 2: down, 0: chain end)
+// and returns true to stop.  Returns 0 at stop, 1 when stopped by on_bend,
+// 2 at the chain end.
+template <typename T, class OnBend>
+__device__ __forceinline__ int lane_scan(LaneState<T>& st, int m, int stop, const T* sv, const T* sa, OnBend on_bend)
+{
+    for (;;) {
+        if (st.i >= stop) return 0;
+        const int i = st.i;
+        const T vi = sv[skew32(i)];
+        const T Ai = (i < m - 1) ? sa[skew32(i)] : T(0);
+        bool init = (i == st.s);
+        if (!init) {
+            st.uh += st.th - vi;
+            st.ul += st.tl - vi;
+            const bool bhi = st.uh < -Ai;
+            const bool blo = !bhi && st.ul > Ai;
+            if (bhi || blo) {
+                const int e = bhi ? st.ih : st.il;
+                const T t = bhi ? st.th : st.tl;
+                st.u0 = bhi ? st.ah : -st.al;
+                const int s_old = st.s;
+                st.s = e + 1;
+                if (on_bend(s_old, e, bhi ? 1 : 2, t)) {
+                    st.i = st.s;
+                    return 1;
+                }
+                if (st.s < i) {
+                    st.i = st.s;
+                    continue;
+                }
+                init = true;
+            } else {
+                const int len = i - st.s + 1;
+                if (st.uh > Ai) {
+                    st.th -= div_len<T>(st.uh - Ai, len);
+                    st.uh = Ai;
+                    st.ih = i;
+                    st.ah = Ai;
+                }
+                if (st.ul < -Ai) {
+                    st.tl += div_len<T>(-Ai - st.ul, len);
+                    st.ul = -Ai;
+                    st.il = i;
+                    st.al = Ai;
+                }
+            }
+        }
+        if (init) {
+            st.th = vi + Ai - st.u0;
+            st.tl = vi - Ai - st.u0;
+            st.uh = Ai;
+            st.ul = -Ai;
+            st.ih = st.il = i;
+            st.ah = st.al = Ai;
+        }
+        if (i == m - 1) {
+            on_bend(st.s, m - 1, 0, st.th);
+            st.i = m;
+            return 2;
+        }
+        st.i = i + 1;
+    }
+}
+
+constexpr int kWarpChains = 8;      // chains (warps) per CTA of the warp scan
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, int nc)
+{
+    extern __shared__ __align__(16) unsigned char wsm[];
+    int k = 0;
+    while (k + 1 < A.naxes && blockIdx.x >= A.ax[k + 1].block_begin) ++k;
+    const ScanAxis<T>& X = A.ax[k];
+    const int m = X.m;
+    const int pitch = skew32(m) + 1;
+    T* sv = (T*)wsm;
+    T* sa = sv + (size_t)nc * pitch;
+    uint8_t* code = (uint8_t*)(sa + (size_t)nc * pitch);
+    const int64_t c0 = (int64_t)(blockIdx.x - X.block_begin) * nc;
+    const int nvalid = (int)min((int64_t)nc, X.nchains - c0);
+
+    auto gbase = [&](int64_t c, int64_t& vb, int64_t& ab, int64_t& st) {
+        if (X.transposed) { vb = c; ab = c; st = X.nchains; }
+        else {
+            const int64_t o = c / X.inner, q = c - o * X.inner;
+            vb = o * (int64_t)m * X.inner + q;
+            ab = o * (int64_t)(m - 1) * X.inner + q;
+            st = X.inner;
+        }
+    };
+    // stage the CTA's chains (chain index fastest: consecutive chains are
+    // consecutive in global memory) and clear the bend codes
+    for (int idx = threadIdx.x; idx < nc * m; idx += blockDim.x) {
+        const int c = idx % nc, j = idx / nc;
+        code[c * m + j] = 0;
+        if (c >= nvalid) continue;
+        int64_t vb, ab, st;
+        gbase(c0 + c, vb, ab, st);
+        scan_cp_elem(sv + c * pitch + skew32(j), X.v + vb + (int64_t)j * st);
+        if (j < m - 1) scan_cp_elem(sa + c * pitch + skew32(j), X.a + ab + (int64_t)j * st);
+    }
+    scan_cp_wait();
+    __syncthreads();
+
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid >= nvalid) return;
+    int64_t vb, ab, gst;
+    gbase(c0 + wid, vb, ab, gst);
+    T* gx = X.x + vb;
+    const T* cv = sv + wid * pitch;
+    const T* ca = sa + wid * pitch;
+    uint8_t* cc = code + wid * m;
+    const int lp = (m + 31) / 32;                 // piece length
+    const int npieces = (m + lp - 1) / lp;
+    const int p0 = lane * lp;
+    const int p1 = min(m, p0 + lp);
+    const bool active = lane < npieces;
+    const bool lastp = lane == npieces - 1;
+    auto write_seg = [&](int from, int to, T t) {
+        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = t;
+    };
+
+    // phase 1: every piece from a guessed state
+    LaneState<T> st{p0, p0, p0, p0, T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    if (active) {
+        lane_scan<T>(st, m, lastp ? m : p1, cv, ca, [&](int s0, int e, int d, T t) {
+            if (d) cc[e] = (uint8_t)d;
+            write_seg(s0, e, t);
+            return false;
+        });
+    }
+    __syncwarp();
+    // phase 2: continue until a bend recorded by a later piece (or the end)
+    int merge = m - 1;
+    if (active && !lastp) {
+        LaneState<T> s2 = st;
+        lane_scan<T>(s2, m, m, cv, ca, [&](int, int e, int d, T) {
+            if (d && e >= p1 && cc[e] == (uint8_t)d) {
+                merge = e;
+                return true;
+            }
+            return false;
+        });
+    }
+    // verified pieces: lane 0, then the piece holding each verified lane's
+    // merge bend (pieces skipped over are rewritten by that continuation)
+    const int target = (active && !lastp && merge < m - 1) ? merge / lp : npieces;
+    unsigned verified = 0;
+    for (int v = 0; v < npieces;) {
+        verified |= 1u << v;
+        v = __shfl_sync(0xffffffffu, target, v);
+    }
+    // phase 3: verified lanes rewrite their continuation up to the merge bend
+    if (((verified >> lane) & 1u) && active && !lastp) {
+        lane_scan<T>(st, m, m, cv, ca, [&](int s0, int e, int, T t) {
+            write_seg(s0, e, t);
+            return e >= merge;
+        });
+    }
+}
+
+template <typename T>
+static size_t wscan_smem(int m, int nc)
+{
+    return (size_t)nc * (2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
+}
+
 template <typename T>
 cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
 {
-    int64_t blocks = 0;
+    // one thread per chain unless the launch has too few chains to fill the
+    // GPU, in which case long chains go to the warp-per-chain scan
+    int64_t total = 0;
+    for (int k = 0; k < A.naxes; ++k) total += A.ax[k].nchains;
+    ScanArgs<T> thr, wrp;
+    thr.naxes = wrp.naxes = 0;
     for (int k = 0; k < A.naxes; ++k) {
-        A.ax[k].block_begin = (unsigned)blocks;
-        blocks += (A.ax[k].nchains + kScanThreads - 1) / kScanThreads;
+        const ScanAxis<T>& X = A.ax[k];
+        bool warp = X.m >= 64 && total < 32768 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        if (A.force == 1) warp = false;
+        if (A.force == 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        if (warp) wrp.ax[wrp.naxes++] = X;
+        else thr.ax[thr.naxes++] = X;
     }
-    if (blocks == 0) return cudaSuccess;
-    scan_kernel<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(A);
-    return cudaGetLastError();
+    if (thr.naxes) {
+        int64_t blocks = 0;
+        for (int k = 0; k < thr.naxes; ++k) {
+            thr.ax[k].block_begin = blocks;
+            blocks += (thr.ax[k].nchains + kScanThreads - 1) / kScanThreads;
+        }
+        if (blocks > 0) {
+            scan_kernel<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (wrp.naxes) {
+        int mmax = 0;
+        for (int k = 0; k < wrp.naxes; ++k) mmax = max(mmax, wrp.ax[k].m);
+        int nc = kWarpChains;
+        while (nc > 1 && wscan_smem<T>(mmax, nc) > 100 * 1024) nc /= 2;
+        int64_t blocks = 0;
+        for (int k = 0; k < wrp.naxes; ++k) {
+            wrp.ax[k].block_begin = blocks;
+            blocks += (wrp.ax[k].nchains + nc - 1) / nc;
+        }
+        const size_t smem = wscan_smem<T>(mmax, nc);
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+            e = cudaFuncSetAttribute(wscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        }
+        if (blocks > 0) {
+            wscan_kernel<T><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
+            return cudaGetLastError();
+        }
+    }
+    return cudaSuccess;
 }
 
 // ---- update -----------------------------------------------------------------

@@ -124,7 +124,7 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP) { why = "params.algo must be TVCUT_AAR or TVCUT_AP"; return false; }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
-    if (p->mapping < -1 || p->mapping > 4) { why = "params.mapping must be -1 (auto) or 0..4"; return false; }
+    if (p->mapping < -1 || p->mapping > 6) { why = "params.mapping must be -1 (auto) or 0..6"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
@@ -159,7 +159,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     h->p = prm;
     h->stream = (cudaStream_t)cuda_stream;
     h->esize = prm.iterate_dtype == TVCUT_F64 ? 8 : 4;
-    h->tlast = prm.mapping <= 0;
+    h->tlast = prm.mapping <= 0 || prm.mapping >= 5;
     memset(&h->last, 0, sizeof(h->last));
     const size_t es = (size_t)h->esize;
     cudaError_t e = cudaSuccess;
@@ -359,6 +359,7 @@ static cudaError_t run_iteration(tvcut_t h, int mode, int check)
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
     S.naxes = r;
+    S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
     for (int k = 0; k < r; ++k) {
         ChainGeom g = chain_geom(h->ndim, h->dims, k);
         S.ax[k].nchains = g.nchains;

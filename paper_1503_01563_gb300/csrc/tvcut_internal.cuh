@@ -38,6 +38,7 @@ struct ScanAxis {
 template <typename T>
 struct ScanArgs {
     int naxes;
+    int force;             // 0 automatic, 1 thread per chain, 2 warp per chain
     ScanAxis<T> ax[3];
 };
 
