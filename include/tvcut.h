@@ -219,6 +219,51 @@ tvcut_status tvcut_profile(tvcut_t h, int enable);
  * tvcut_profile call; counted always).  Synchronises h's stream. */
 tvcut_status tvcut_profile_read(tvcut_t h, double* ms, int64_t* launches);
 
+/* ---- Batched grids -------------------------------------------------------
+ * Many independent 2D grids of different sizes solved together (the method
+ * above on each grid; the grids share nothing).  One iteration of every grid
+ * is one chain-prox launch over all chains of all grids (persistent CTAs
+ * taking work items, longest chains first) and one update launch over all
+ * vertices; each tvcut_batch_iterate call (its iterations and the closing
+ * check) runs as one CUDA graph, captured on first use for that iteration
+ * count and replayed afterwards.  Parameters as for tvcut_create (mapping is
+ * ignored; tvcut_batch_autotune picks the launch shape). */
+typedef struct tvcut_batch_ctx* tvcut_batch_t;
+
+/* G grids; dims holds G pairs {H_g, W_g} (1 <= H_g, W_g <= 2^20).  Allocates
+ * about 8 arrays of sum_g H_g W_g values.  Errors: INVALID, OOM, CUDA. */
+tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvcut_params* p,
+                                void* cuda_stream, tvcut_batch_t* out);
+void tvcut_batch_destroy(tvcut_batch_t b);
+const char* tvcut_batch_last_error(tvcut_batch_t b);
+
+/* Inputs of grid g, as tvcut_set_unary / tvcut_set_weights (axis 0: the
+ * (H-1) x W vertical weights, axis 1: the H x (W-1) horizontal weights). */
+tvcut_status tvcut_batch_set_unary(tvcut_batch_t b, int g, const void* w, int dtype,
+                                   int space);
+tvcut_status tvcut_batch_set_weights(tvcut_batch_t b, int g, int axis, const void* a,
+                                     int dtype, int space);
+
+/* Cold start of every grid (as tvcut_reset).  Errors: STATE, CUDA. */
+tvcut_status tvcut_batch_reset(tvcut_batch_t b);
+
+/* Exactly `iters` iterations of every grid, then a check of every grid
+ * (labels, energy, bounds, level sets).  out: NULL or G tvcut_stats.
+ * Returns OK if every grid is certified, NOT_CONVERGED otherwise. */
+tvcut_status tvcut_batch_iterate(tvcut_batch_t b, int64_t iters, tvcut_stats* out);
+
+/* Labels (H_g x W_g uint8) and statistics of grid g after the last check. */
+tvcut_status tvcut_batch_cut(tvcut_batch_t b, int g, uint8_t* labels, int space,
+                             tvcut_stats* out);
+
+/* Product-space state of grid g (2 x H_g x W_g values of the iterate type). */
+tvcut_status tvcut_batch_get_state(tvcut_batch_t b, int g, void* s, int space);
+
+/* Time the chain-prox launch for CTA sizes {64, 128, 256} and {4, 8, 16}
+ * CTAs per SM on the current inputs and keep the fastest; chosen (may be
+ * NULL) receives {threads, ctas_per_sm}.  Results do not depend on it. */
+tvcut_status tvcut_batch_autotune(tvcut_batch_t b, int* chosen);
+
 /* Iterations without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot let a library allocate
  * device memory -- code whose framework allocator owns all of the GPU's

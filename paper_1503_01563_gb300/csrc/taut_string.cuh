@@ -1,0 +1,90 @@
+// The taut-string scan of one chain (Sec. 3.2), shared by every kernel that
+// runs it: the per-thread chain prox of the scan launches, single grid and
+// batched.
+#pragma once
+#include <stdint.h>
+
+namespace tvcut {
+
+// Taut-string scan of one chain: element j of v at v[j*stride], weight of
+// edge (j, j+1) at a[j*stride]; writes x[j*stride] = prox value.  From a
+// segment start s with incoming multiplier u0, a common value t on s..i gives
+// u_i = u0 + sum_{j=s..i} (t - v_j), which must stay in [-a_i, a_i] (and be 0
+// at the chain end).  th/tl are the largest/smallest feasible t and uh/ul the
+// matching u_i; when the feasible set empties, the segment ends at the point
+// that last limited the violated bound (the string bends there) and the scan
+// resumes after it.  Pointers advance by `stride` per element; only a rescan
+// recomputes them.
+template <typename T>
+__device__ __forceinline__ T div_len(T num, int len)
+{
+    if constexpr (sizeof(T) == 4) return num * __frcp_rn((float)len);   // 1/len correctly rounded
+    else return num / (T)len;
+}
+
+template <typename T>
+__device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const T* __restrict__ a,
+                                           T* __restrict__ x, int64_t stride)
+{
+    int s = 0, i = 0, ih = 0, il = 0;
+    T u0 = T(0), th = T(0), tl = T(0), uh = T(0), ul = T(0), ah = T(0), al = T(0);
+    const T* pv = v;
+    const T* pa = a;
+    T* px = x;                                   // next element to write
+    for (;;) {
+        const T vi = *pv;
+        const T Ai = (i < m - 1) ? *pa : T(0);
+        bool init = (i == s);
+        if (!init) {
+            uh += th - vi;
+            ul += tl - vi;
+            const bool bhi = uh < -Ai;
+            const bool blo = !bhi && ul > Ai;
+            if (bhi || blo) {                        // the string bends at e
+                const int e = bhi ? ih : il;
+                const T t = bhi ? th : tl;
+                u0 = bhi ? ah : -al;
+                for (int j = s; j <= e; ++j, px += stride) *px = t;
+                s = e + 1;
+                if (s < i) {                         // rescan from the bend
+                    i = s;
+                    pv = v + (int64_t)s * stride;
+                    pa = a + (int64_t)s * stride;
+                    continue;
+                }
+                init = true;                         // the new segment starts at i
+            } else {
+                const int len = i - s + 1;
+                if (uh > Ai) {
+                    th -= div_len<T>(uh - Ai, len);
+                    uh = Ai;
+                    ih = i;
+                    ah = Ai;
+                }
+                if (ul < -Ai) {
+                    tl += div_len<T>(-Ai - ul, len);
+                    ul = -Ai;
+                    il = i;
+                    al = Ai;
+                }
+            }
+        }
+        if (init) {
+            th = vi + Ai - u0;
+            tl = vi - Ai - u0;
+            uh = Ai;
+            ul = -Ai;
+            ih = il = i;
+            ah = al = Ai;
+        }
+        if (i == m - 1) {
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
+            break;
+        }
+        ++i;
+        pv += stride;
+        pa += stride;
+    }
+}
+
+}  // namespace tvcut

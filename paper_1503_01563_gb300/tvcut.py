@@ -28,6 +28,9 @@ EXPORTED = [
     "tvcut_set_unary", "tvcut_set_weights", "tvcut_reset", "tvcut_iterate", "tvcut_cut",
     "tvcut_get_primal", "tvcut_get_state", "tvcut_set_state", "tvcut_warmstart_primal",
     "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc",
+    "tvcut_batch_create", "tvcut_batch_destroy", "tvcut_batch_last_error", "tvcut_batch_set_unary",
+    "tvcut_batch_set_weights", "tvcut_batch_reset", "tvcut_batch_iterate", "tvcut_batch_cut",
+    "tvcut_batch_get_state", "tvcut_batch_autotune",
 ]
 K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
@@ -97,6 +100,16 @@ def load(path: str = LIB_PATH):
         "tvcut_profile": (st, [P, c_int]),
         "tvcut_profile_read": (st, [P, P, P]),
         "tvcut_iterate_noalloc": (st, [c_int, P, c_int, c_int, P, P, P, P, i64, P]),
+        "tvcut_batch_create": (st, [c_int, P, ctypes.POINTER(Params), P, ctypes.POINTER(P)]),
+        "tvcut_batch_destroy": (None, [P]),
+        "tvcut_batch_last_error": (ctypes.c_char_p, [P]),
+        "tvcut_batch_set_unary": (st, [P, c_int, P, c_int, c_int]),
+        "tvcut_batch_set_weights": (st, [P, c_int, c_int, P, c_int, c_int]),
+        "tvcut_batch_reset": (st, [P]),
+        "tvcut_batch_iterate": (st, [P, i64, P]),
+        "tvcut_batch_cut": (st, [P, c_int, P, c_int, ctypes.POINTER(Stats)]),
+        "tvcut_batch_get_state": (st, [P, c_int, P, c_int]),
+        "tvcut_batch_autotune": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -329,3 +342,73 @@ class Solver:
     def set_state(self, s):
         want = np.float64 if self.dtype == F64 else np.float32
         tvcut_set_state(self.h, np.ascontiguousarray(s, dtype=want))
+
+
+def _bcheck(code, b):
+    if code < 0:
+        msg = lib().tvcut_batch_last_error(b)
+        raise TvcutError(code, msg.decode() if msg else "")
+    return code
+
+
+class Batch:
+    """Many independent 2D grids iterated together (tvcut_batch_*)."""
+
+    def __init__(self, dims_list, algo=AAR, dtype=F32, threshold=0.0, level_sets=None, stream=None):
+        p = tvcut_default_params()
+        p.algo = algo
+        p.iterate_dtype = dtype
+        p.threshold = threshold
+        if level_sets is not None:
+            p.level_sets = level_sets
+        self.dims = [(int(h), int(w)) for h, w in dims_list]
+        self.G = len(self.dims)
+        self.dtype = dtype
+        flat = (ctypes.c_int64 * (2 * self.G))(*[v for hw in self.dims for v in hw])
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream) if stream else 0)
+        _bcheck(lib().tvcut_batch_create(self.G, flat, ctypes.byref(p), s, ctypes.byref(h)), None)
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().tvcut_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_problem(self, g, w, a):
+        pw, sw, dw, kw = _buf(w)
+        _bcheck(lib().tvcut_batch_set_unary(self.h, int(g), pw, dw, sw), self.h)
+        for k, ak in enumerate(a):
+            pa, sa, da, ka = _buf(ak)
+            _bcheck(lib().tvcut_batch_set_weights(self.h, int(g), k, pa, da, sa), self.h)
+
+    def reset(self):
+        _bcheck(lib().tvcut_batch_reset(self.h), self.h)
+
+    def iterate(self, iters):
+        out = (Stats * self.G)()
+        code = _bcheck(lib().tvcut_batch_iterate(self.h, int(iters), out), self.h)
+        return code, list(out)
+
+    def cut(self, g):
+        lab = np.empty(self.dims[g], dtype=np.uint8)
+        st = Stats()
+        _bcheck(lib().tvcut_batch_cut(self.h, int(g), ctypes.c_void_p(lab.ctypes.data), HOST, ctypes.byref(st)),
+                self.h)
+        return lab, st
+
+    def state(self, g):
+        s = np.empty((2,) + self.dims[g], dtype=np.float64 if self.dtype == F64 else np.float32)
+        _bcheck(lib().tvcut_batch_get_state(self.h, int(g), ctypes.c_void_p(s.ctypes.data), HOST), self.h)
+        return s
+
+    def autotune(self):
+        ch = (ctypes.c_int * 2)()
+        _bcheck(lib().tvcut_batch_autotune(self.h, ch), self.h)
+        return int(ch[0]), int(ch[1])
