@@ -264,6 +264,48 @@ tvcut_status tvcut_batch_get_state(tvcut_batch_t b, int g, void* s, int space);
  * NULL) receives {threads, ctas_per_sm}.  Results do not depend on it. */
 tvcut_status tvcut_batch_autotune(tvcut_batch_t b, int* chosen);
 
+/* ---- Learned warm start -------------------------------------------------
+ * A U-Net (4 levels, `base` channels at full resolution, 3x3 convolutions
+ * with ReLU, 2x2 average pooling, nearest 2x upsampling, skip
+ * concatenations) with BF16 weights/activations and FP32 accumulation and
+ * master weights, trained on the GPU by its own forward/backward kernels and
+ * Adam.  It maps a 2D problem to the per-block dual variables y_0, y_1 of the
+ * product-space iteration; a solver started from z = y_hat (tvcut_set_state)
+ * begins from the predicted iterate instead of 0 (the warm start of Sec.
+ * 4.4 reuses dual variables).  Input: batch x H x W x 3 FP32 (caller-
+ * normalised w, vertical and horizontal weight of each vertex); output:
+ * batch x H x W x 2 FP32.  H and W must be multiples of 8.  Parameters are
+ * one FP32 vector: for each of the 18 convolutions in forward order, weights
+ * [9][Cout][Cin] (tap 3*ky + kx reads pixel (y+ky-1, x+kx-1)) then bias
+ * [Cout]. */
+typedef struct tvcut_unet_ctx* tvcut_unet_t;
+
+tvcut_status tvcut_unet_create(int base, int batch, int H, int W, uint64_t seed,
+                               void* cuda_stream, tvcut_unet_t* out);
+void tvcut_unet_destroy(tvcut_unet_t u);
+const char* tvcut_unet_last_error(tvcut_unet_t u);
+/* Reallocate activations for a new batch/size (parameters kept). */
+tvcut_status tvcut_unet_resize(tvcut_unet_t u, int batch, int H, int W);
+/* in, out: DEVICE pointers; out may be NULL (keeps the result internal). */
+tvcut_status tvcut_unet_forward(tvcut_unet_t u, const float* in, float* out);
+/* After a forward: MSE loss against target (DEVICE, batch x H x W x 2),
+ * parameter gradients (overwritten), loss to *loss (host, may be NULL). */
+tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target, float* loss);
+/* One Adam step on the FP32 master weights. */
+tvcut_status tvcut_unet_adam(tvcut_unet_t u, float lr, float beta1, float beta2, float eps);
+tvcut_status tvcut_unet_num_params(tvcut_unet_t u, int64_t* count);
+/* which = 0: parameters, 1: last gradients; dst is HOST memory. */
+tvcut_status tvcut_unet_get_params(tvcut_unet_t u, float* dst, int which);
+tvcut_status tvcut_unet_set_params(tvcut_unet_t u, const float* src);
+/* Single-layer kernels (DEVICE, BF16 as raw 16-bit words, NHWC, channels
+ * multiples of 16): out = relu?(bias + conv3x3(in, wt)) with wt
+ * [9][Cout][Cin]; dw[9][Cout][Cin] += sum_p dout[p][co] in[p + tap][ci]. */
+tvcut_status tvcut_conv3x3_bf16(const void* in, const void* wt, const float* bias, void* out,
+                                int N, int H, int W, int Cin, int Cout, int relu,
+                                void* cuda_stream);
+tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dout, float* dw, int N,
+                                      int H, int W, int Cin, int Cout, void* cuda_stream);
+
 /* Iterations without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot let a library allocate
  * device memory -- code whose framework allocator owns all of the GPU's

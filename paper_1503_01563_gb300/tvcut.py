@@ -31,6 +31,9 @@ EXPORTED = [
     "tvcut_batch_create", "tvcut_batch_destroy", "tvcut_batch_last_error", "tvcut_batch_set_unary",
     "tvcut_batch_set_weights", "tvcut_batch_reset", "tvcut_batch_iterate", "tvcut_batch_cut",
     "tvcut_batch_get_state", "tvcut_batch_autotune",
+    "tvcut_unet_create", "tvcut_unet_destroy", "tvcut_unet_last_error", "tvcut_unet_resize",
+    "tvcut_unet_forward", "tvcut_unet_backward", "tvcut_unet_adam", "tvcut_unet_num_params",
+    "tvcut_unet_get_params", "tvcut_unet_set_params", "tvcut_conv3x3_bf16", "tvcut_conv3x3_wgrad_bf16",
 ]
 K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
@@ -110,6 +113,18 @@ def load(path: str = LIB_PATH):
         "tvcut_batch_cut": (st, [P, c_int, P, c_int, ctypes.POINTER(Stats)]),
         "tvcut_batch_get_state": (st, [P, c_int, P, c_int]),
         "tvcut_batch_autotune": (st, [P, P]),
+        "tvcut_unet_create": (st, [c_int, c_int, c_int, c_int, ctypes.c_uint64, P, ctypes.POINTER(P)]),
+        "tvcut_unet_destroy": (None, [P]),
+        "tvcut_unet_last_error": (ctypes.c_char_p, [P]),
+        "tvcut_unet_resize": (st, [P, c_int, c_int, c_int]),
+        "tvcut_unet_forward": (st, [P, P, P]),
+        "tvcut_unet_backward": (st, [P, P, ctypes.POINTER(ctypes.c_float)]),
+        "tvcut_unet_adam": (st, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "tvcut_unet_num_params": (st, [P, ctypes.POINTER(i64)]),
+        "tvcut_unet_get_params": (st, [P, P, c_int]),
+        "tvcut_unet_set_params": (st, [P, P]),
+        "tvcut_conv3x3_bf16": (st, [P, P, P, P, c_int, c_int, c_int, c_int, c_int, c_int, P]),
+        "tvcut_conv3x3_wgrad_bf16": (st, [P, P, P, c_int, c_int, c_int, c_int, c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -412,3 +427,67 @@ class Batch:
         ch = (ctypes.c_int * 2)()
         _bcheck(lib().tvcut_batch_autotune(self.h, ch), self.h)
         return int(ch[0]), int(ch[1])
+
+
+def _ucheck(code, u):
+    if code < 0:
+        msg = lib().tvcut_unet_last_error(u)
+        raise TvcutError(code, msg.decode() if msg else "")
+    return code
+
+
+class UNet:
+    """The warm-start network (tvcut_unet_*).  Tensors are CUDA float32."""
+
+    def __init__(self, base=32, batch=1, H=64, W=64, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream) if stream else 0)
+        _ucheck(lib().tvcut_unet_create(int(base), int(batch), int(H), int(W), ctypes.c_uint64(seed), s,
+                                        ctypes.byref(h)), None)
+        self.h = h
+        self.shape = (batch, H, W)
+        n = ctypes.c_int64()
+        _ucheck(lib().tvcut_unet_num_params(self.h, ctypes.byref(n)), self.h)
+        self.nparams = int(n.value)
+
+    def close(self):
+        if self.h:
+            lib().tvcut_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def resize(self, batch, H, W):
+        _ucheck(lib().tvcut_unet_resize(self.h, int(batch), int(H), int(W)), self.h)
+        self.shape = (batch, H, W)
+
+    def forward(self, x, out=None):
+        """x: (batch, H, W, 3) float32 CUDA tensor; returns (batch, H, W, 2)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.shape + (2,), dtype=torch.float32, device=x.device)
+        _ucheck(lib().tvcut_unet_forward(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+                self.h)
+        return out
+
+    def backward(self, target):
+        loss = ctypes.c_float()
+        _ucheck(lib().tvcut_unet_backward(self.h, ctypes.c_void_p(target.data_ptr()), ctypes.byref(loss)), self.h)
+        return float(loss.value)
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _ucheck(lib().tvcut_unet_adam(self.h, lr, beta1, beta2, eps), self.h)
+
+    def params(self, which=0):
+        out = np.empty(self.nparams, dtype=np.float32)
+        _ucheck(lib().tvcut_unet_get_params(self.h, ctypes.c_void_p(out.ctypes.data), int(which)), self.h)
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        _ucheck(lib().tvcut_unet_set_params(self.h, ctypes.c_void_p(p.ctypes.data)), self.h)

@@ -1,0 +1,110 @@
+"""Warm-start network kernels against the CPU oracle (oracle/unet_ref.py,
+PyTorch CPU FP32).  The GPU computes with BF16 weights and activations and
+FP32 accumulation, so results are compared by relative L2 error: 2e-2 for a
+single convolution, 5e-2 for the 18-layer forward pass, 1e-1 for parameter
+gradients (BF16 activation gradients through 18 layers)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_01563_gb300 import tvcut
+    tvcut.lib()
+    return tvcut
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def bf16_round(x):
+    return torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).float().numpy()
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 16, 16, 32), (2, 9, 13, 32, 16), (1, 8, 8, 64, 128)])
+def test_conv_forward_and_wgrad(tv, shape):
+    from oracle import unet_ref
+    n, h, w, ci, co = shape
+    rng = np.random.default_rng(sum(shape))
+    x = bf16_round(rng.normal(size=(n, h, w, ci)))
+    wk = bf16_round(rng.normal(size=(9, co, ci)) * 0.2)
+    b = rng.normal(size=co).astype(np.float32)
+    xd = torch.tensor(x).to(torch.bfloat16).cuda()
+    wd = torch.tensor(wk).to(torch.bfloat16).cuda()
+    bd = torch.tensor(b).cuda()
+    out = torch.empty((n, h, w, co), dtype=torch.bfloat16, device="cuda")
+    tv.lib().tvcut_conv3x3_bf16(xd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(), n, h, w, ci, co, 1, None)
+    torch.cuda.synchronize()
+    W = torch.tensor(wk, requires_grad=True)
+    Wt = W.reshape(3, 3, co, ci).permute(2, 3, 0, 1)
+    xt = torch.tensor(x).permute(0, 3, 1, 2)
+    ref = torch.relu(unet_ref.F.conv2d(xt, Wt, torch.tensor(b), padding=1)).permute(0, 2, 3, 1)
+    assert rel(out.float().cpu().numpy(), ref.detach().numpy()) < 2e-2
+    # weight gradient of sum(ref * g) for a random g (before the ReLU: use the linear conv)
+    g = bf16_round(rng.normal(size=(n, h, w, co)))
+    lin = unet_ref.F.conv2d(xt, Wt, None, padding=1).permute(0, 2, 3, 1)
+    (lin * torch.tensor(g)).sum().backward()
+    dw = torch.zeros((9, co, ci), dtype=torch.float32, device="cuda")
+    gd = torch.tensor(g).to(torch.bfloat16).cuda()
+    tv.lib().tvcut_conv3x3_wgrad_bf16(xd.data_ptr(), gd.data_ptr(), dw.data_ptr(), n, h, w, ci, co, None)
+    torch.cuda.synchronize()
+    assert rel(dw.cpu().numpy(), W.grad.numpy()) < 2e-2
+
+
+def test_network_forward_backward(tv):
+    from oracle import unet_ref
+    base, n, h, w = 32, 2, 32, 24
+    net = tv.UNet(base=base, batch=n, H=h, W=w, seed=7)
+    theta = net.params()
+    assert theta.size == unet_ref.num_params(base)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(n, h, w, 3)).astype(np.float32)
+    t = rng.normal(size=(n, h, w, 2)).astype(np.float32)
+    out = net.forward(torch.tensor(x).cuda())
+    loss = net.backward(torch.tensor(t).cuda())
+    grad = net.params(which=1)
+    theta_bf = bf16_round(theta)                 # the forward pass uses BF16 weights
+    ref_loss, ref_grad, ref_out = unet_ref.loss_and_grad(theta_bf, bf16_round(x), t, base)
+    assert rel(out.cpu().numpy(), ref_out) < 5e-2
+    assert abs(loss - ref_loss) < 5e-2 * ref_loss
+    assert rel(grad, ref_grad) < 1e-1
+    # per-layer gradient direction
+    off = 0
+    for ci, co in unet_ref.layer_shapes(base):
+        k = 9 * ci * co + co
+        gl, rl = grad[off:off + k], ref_grad[off:off + k]
+        cos = float(gl @ rl / (np.linalg.norm(gl) * np.linalg.norm(rl) + 1e-30))
+        assert cos > 0.98, (ci, co, cos)
+        off += k
+    net.close()
+
+
+def test_training_reduces_loss(tv):
+    net = tv.UNet(base=32, batch=4, H=32, W=32, seed=11)
+    rng = np.random.default_rng(4)
+    x = torch.tensor(rng.normal(size=(4, 32, 32, 3)).astype(np.float32)).cuda()
+    # a smooth, learnable target: local averages of the input channels
+    xt = x.permute(0, 3, 1, 2)
+    t = torch.nn.functional.avg_pool2d(xt[:, :2], 3, stride=1, padding=1).permute(0, 2, 3, 1).contiguous()
+    losses = []
+    for _ in range(150):
+        net.forward(x)
+        losses.append(net.backward(t))
+        net.adam(lr=2e-3)
+    assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+    net.close()
+
+
+def test_params_roundtrip(tv):
+    net = tv.UNet(base=16, batch=1, H=16, W=16, seed=1)
+    p = net.params()
+    net.set_params(p * 0.5)
+    np.testing.assert_array_equal(net.params(), (p * 0.5).astype(np.float32))
+    net.close()
