@@ -37,6 +37,9 @@ WORKLOADS = {
     "seg1024": dict(dims=(1024, 1024), seed=2, cap=3000),
     # 512 independent 2D grids, H ~ U{64..1024} x W ~ U{64..768}, w ~ U{-50..50}, a ~ U{1..20}
     "batch512": dict(grids=512, seed=4, cap=3000),
+    # learned warm start: U-Net (4 levels, 32 channels) trained on solver-generated 128^2 problems,
+    # evaluated on held-out 2048^2 problems (w ~ U{-50..50}, a ~ U{1..20}), cold vs warm
+    "warm2048": dict(dims=(2048, 2048), seed=999, cap=3000, train_n=4096, train_hw=128, train_steps=1500),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -47,6 +50,8 @@ def make_problem(name):
         dims, probs = batch_problems(wl["grids"], wl["seed"])
         g = max(range(len(dims)), key=lambda i: dims[i][0] * dims[i][1])
         return probs[g]
+    if name == "warm2048":
+        return inputs.uniform_grid(wl["dims"], wl["seed"])
     if len(wl["dims"]) == 3:
         return inputs.volume_problem(wl["dims"], wl["seed"])
     return inputs.segmentation_problem(wl["dims"], wl["seed"])
@@ -348,6 +353,106 @@ def run_batch(args):
     return 0
 
 
+def run_warm(args):
+    """Cold-started AAR vs AAR started from the U-Net's predicted block duals,
+    both to the oracle-equal cut, on one GPU."""
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank != 0:
+        return 0                                   # single-GPU workload: extra ranks idle
+    torch.cuda.set_device(local)
+    from paper_1503_01563_gb300 import learn, tvcut
+    wl = WORKLOADS["warm2048"]
+    dims = wl["dims"]
+    w, a = inputs.uniform_grid(dims, wl["seed"])
+    n = int(np.prod(dims))
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    e_star = oracle.maxflow(w, a, 1)[1]
+    t_mf = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    st0 = oracle.cold_state(oracle.AAR, w)
+    t0 = time.perf_counter()
+    oracle.iterate(oracle.AAR, w, a, st0, 2, nthreads=cores)
+    t_it = time.perf_counter() - t0
+    cpu_base = {"value": 2 * n / t_it / 1e6, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
+                "sample": f"2 FP64 AAR iterations over the 2048^2 grid ({t_it:.1f} s); max-flow E* {t_mf:.1f} s"}
+    stream = torch.cuda.current_stream()
+    # training (untimed): solver-generated targets, GPU forward/backward/Adam
+    t0 = time.perf_counter()
+    X, Y = learn.make_training_set(wl["train_n"], wl["train_hw"], wl["train_hw"], seed=1)
+    t_data = time.perf_counter() - t0
+    net = tvcut.UNet(base=32, batch=16, H=wl["train_hw"], W=wl["train_hw"], seed=3, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    hist = learn.train(net, X, Y, steps=wl["train_steps"], batch=16)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, Y
+    s = tvcut.Solver(dims, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+    s.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
+
+    def probe(z0):
+        if z0 is None:
+            s.reset()
+        else:
+            tvcut.tvcut_set_state(s.h, z0)
+        for k in range(1, wl["cap"] + 1):
+            _, st = s.iterate(1)
+            if st.energy_i64 == e_star:
+                return k
+        return None
+    k_cold = probe(None)
+    z0 = learn.predict_state(net, w, a)
+    k_warm = probe(z0)
+    timed = tvcut.Solver(dims, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream)
+    timed.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
+    feats = torch.from_numpy(learn.features(w, a)[0][None]).cuda()
+    sc = learn.features(w, a)[1]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    cold_ms, warm_ms, inf_ms, ok = [], [], [], True
+    for rep in range(args.warmup + args.steps):
+        ev[0].record(stream)
+        timed.reset()
+        _, st = timed.iterate(k_cold or wl["cap"])
+        ev[1].record(stream)
+        ok = ok and st.energy_i64 == e_star
+        out = net.forward(feats)
+        zw = (out[0].permute(2, 0, 1) * sc).contiguous()
+        ev[2].record(stream)
+        tvcut.tvcut_set_state(timed.h, zw)
+        _, st = timed.iterate(k_warm or wl["cap"])
+        ev[3].record(stream)
+        ev[3].synchronize()
+        ok = ok and st.energy_i64 == e_star
+        if rep >= args.warmup:
+            cold_ms.append(ev[0].elapsed_time(ev[1]))
+            inf_ms.append(ev[1].elapsed_time(ev[2]))
+            warm_ms.append(ev[1].elapsed_time(ev[3]))
+    cold = float(np.median(cold_ms))
+    warm = float(np.median(warm_ms))
+    out = {"metric": "Mvertex-iter/s", "value": n * (k_cold or wl["cap"]) / (cold / 1e3) / 1e6,
+           "unit": "Mvertex-iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": cold,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "warm2048", "dims": list(dims), "algo": "AAR", "iterate": "f32",
+                      "network": "U-Net 4 levels, 32 channels, BF16 weights/activations, FP32 accumulation",
+                      "training": f"{wl['train_n']} solver-generated {wl['train_hw']}^2 problems, "
+                                  f"{wl['train_steps']} Adam steps of 16 (data {t_data:.1f} s, training {t_train:.1f} s, "
+                                  f"loss {hist[0]:.4f} -> {float(np.mean(hist[-20:])):.4f})"},
+           "time_to_oracle_equal_cut_ms": {"cold": cold if k_cold else None, "warm": warm if k_warm else None,
+                                           "warm_inference": float(np.median(inf_ms))},
+           "iters_to_oracle_equal_cut": {"cold": k_cold, "warm": k_warm}, "oracle_min_cut": e_star,
+           "step_energies_match": ok, "cpu_baseline": cpu_base,
+           "roofline": None, "e2e": None, "clocks": None, "gpu_launches": None}
+    print(json.dumps(out), flush=True)
+    s.close()
+    timed.close()
+    net.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -514,6 +619,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "warm2048":
+        return run_warm(args)
     return run_ours(args)
 
 

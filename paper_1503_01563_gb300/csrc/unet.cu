@@ -426,8 +426,8 @@ static tvcut_status run_conv(tvcut_unet_t u, int ci, const Act& in, Act& out, co
     A.CoutStride = c.cout;
     A.relu = c.relu;
     const int64_t P = (int64_t)A.N * A.H * A.W;
-    dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((c.cout + BN - 1) / BN));
-    conv3x3_fwd_kernel<<<grid, 128, 0, u->stream>>>(A);
+    dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((c.cout + BN - 1) / BN));
+    conv3x3_fwd_kernel<<<grid, FTHREADS, 0, u->stream>>>(A);
     UCK(u, cudaGetLastError(), "conv forward");
     return TVCUT_OK;
 }
@@ -538,8 +538,8 @@ static tvcut_status conv_backward(tvcut_unet_t u, int ci, const Act& in, const A
         A.Cout = c.cin;
         A.CoutStride = c.cin;
         A.relu = 0;
-        dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((c.cin + BN - 1) / BN));
-        conv3x3_fwd_kernel<<<grid, 128, 0, u->stream>>>(A);
+        dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((c.cin + BN - 1) / BN));
+        conv3x3_fwd_kernel<<<grid, FTHREADS, 0, u->stream>>>(A);
     }
     UCK(u, cudaGetLastError(), "conv backward");
     return TVCUT_OK;
@@ -691,8 +691,8 @@ extern "C" tvcut_status tvcut_conv3x3_bf16(const void* in, const void* wt, const
     A.CoutStride = Cout;
     A.relu = relu;
     const int64_t P = (int64_t)N * H * W;
-    dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((Cout + BN - 1) / BN));
-    conv3x3_fwd_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(A);
+    dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((Cout + BN - 1) / BN));
+    conv3x3_fwd_kernel<<<grid, FTHREADS, 0, (cudaStream_t)stream>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ufail(nullptr, TVCUT_ERR_CUDA, cudaGetErrorString(e));
     return TVCUT_OK;

@@ -60,49 +60,93 @@ struct ConvArgs {
 };
 
 // out[p][co] = act(bias[co] + sum_k sum_ci in[p + off_k][ci] * wt[k][co][ci])
-__global__ void __launch_bounds__(128) conv3x3_fwd_kernel(ConvArgs A)
+//
+// CTA tile: 128 pixels x 64 output channels, 8 warps (16 pixels x 64 channels
+// each).  The reduction runs over "slices" (one tap, 16 input channels); two
+// slices form a stage, staged into shared memory by 16-byte cp.async copies
+// (zero-filled outside the image) in a two-deep pipeline, so the next stage
+// loads while the tensor cores work on the current one.
+constexpr int FBM = 128;
+constexpr int FTHREADS = 256;
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][SROW];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][SROW];
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;                  // 0 bytes read: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(FTHREADS) conv3x3_fwd_kernel(ConvArgs A)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[2][2][FBM][SROW];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][2][BN][SROW];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t P = (int64_t)A.N * A.H * A.W;
-    const int64_t p0 = (int64_t)blockIdx.x * BM;
+    const int64_t p0 = (int64_t)blockIdx.x * FBM;
     const int n0 = blockIdx.y * BN;
+    const int cslices = A.Cin / BK;
+    const int nslices = 9 * cslices;
+    const int nstages = (nslices + 1) / 2;
+    // A loads: 128 pixels x 2 slices x 2 halves = 512 16-byte copies, 2 per thread
+    int apix[2], ay[2], ax[2];
+    int64_t an[2];
+    bool aval[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int idx = tid + r * FTHREADS;
+        apix[r] = idx >> 2;
+        const int64_t p = p0 + apix[r];
+        aval[r] = p < P;
+        const int64_t pp = aval[r] ? p : 0;
+        ax[r] = (int)(pp % A.W);
+        const int64_t q = pp / A.W;
+        ay[r] = (int)(q % A.H);
+        an[r] = q / A.H;
+    }
+    auto load_stage = [&](int t, int buf) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + r * FTHREADS;
+            const int j = (idx >> 1) & 1, h = idx & 1;
+            const int sl = 2 * t + j;
+            const int k = sl / cslices, c0 = (sl - k * cslices) * BK;
+            const int yy = ay[r] + k / 3 - 1, xx = ax[r] + k % 3 - 1;
+            const bool ok = aval[r] && sl < nslices && yy >= 0 && yy < A.H && xx >= 0 && xx < A.W;
+            const __nv_bfloat16* src = ok ? A.in + ((an[r] * A.H + yy) * A.W + xx) * A.Cin + c0 + 8 * h : A.in;
+            cp16(&As[buf][j][apix[r]][8 * h], src, ok);
+        }
+        {   // B: 64 channels x 2 slices x 2 halves = 256 copies, 1 per thread
+            const int co = tid >> 2, j = (tid >> 1) & 1, h = tid & 1;
+            const int sl = 2 * t + j;
+            const int k = sl / cslices, c0 = (sl - k * cslices) * BK;
+            const bool ok = sl < nslices && n0 + co < A.Cout;
+            const __nv_bfloat16* src = ok ? A.wt + ((int64_t)k * A.Cout + n0 + co) * A.Cin + c0 + 8 * h : A.wt;
+            cp16(&Bs[buf][j][co][8 * h], src, ok);
+        }
+        cp_commit();
+    };
     float acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    // this thread's A-load pixel and half slice
-    const int ap = tid >> 1, ah = tid & 1;
-    const int64_t pa = p0 + ap;
-    int py = 0, px = 0;
-    int64_t pn = 0;
-    if (pa < P) {
-        px = (int)(pa % A.W);
-        const int64_t q = pa / A.W;
-        py = (int)(q % A.H);
-        pn = q / A.H;
-    }
-    // this thread's B-load channel row and half slice
-    const int bc = tid >> 1, bh = tid & 1;
-    for (int k = 0; k < 9; ++k) {
-        const int dy = k / 3 - 1, dx = k % 3 - 1;
-        const int yy = py + dy, xx = px + dx;
-        const bool inside = pa < P && yy >= 0 && yy < A.H && xx >= 0 && xx < A.W;
-        const __nv_bfloat16* src = A.in + (((pn * A.H + yy) * A.W + xx) * A.Cin);
-        for (int c0 = 0; c0 < A.Cin; c0 += BK) {
-            uint4 va = make_uint4(0, 0, 0, 0);
-            if (inside) va = *(const uint4*)(src + c0 + 8 * ah);
-            *(uint4*)&As[ap][8 * ah] = va;
-            uint4 vb = make_uint4(0, 0, 0, 0);
-            if (n0 + bc < A.Cout) vb = *(const uint4*)(A.wt + ((int64_t)k * A.Cout + n0 + bc) * A.Cin + c0 + 8 * bh);
-            *(uint4*)&Bs[bc][8 * bh] = vb;
-            __syncthreads();
-            warp_tile_mma(As, Bs, acc, warp, lane);
-            __syncthreads();
+    load_stage(0, 0);
+    for (int t = 0; t < nstages; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nstages) {
+            load_stage(t + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
+        __syncthreads();
+        warp_tile_mma(As[buf][0], Bs[buf][0], acc, warp, lane);
+        if (2 * t + 1 < nslices) warp_tile_mma(As[buf][1], Bs[buf][1], acc, warp, lane);
+        __syncthreads();
     }
     // epilogue: rows warp*16 + g (+8), columns nt*8 + 2t (+1)
-    const int g = lane >> 2, t = lane & 3;
+    const int g = lane >> 2, tq = lane & 3;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int64_t p = p0 + warp * 16 + g + 8 * half;
@@ -111,7 +155,7 @@ __global__ void __launch_bounds__(128) conv3x3_fwd_kernel(ConvArgs A)
         for (int nt = 0; nt < 8; ++nt) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int co = n0 + nt * 8 + 2 * t + j;
+                const int co = n0 + nt * 8 + 2 * tq + j;
                 if (co >= A.Cout) continue;
                 float v = acc[nt][2 * half + j];
                 if (A.bias) v += A.bias[co];
