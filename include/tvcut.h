@@ -259,9 +259,11 @@ tvcut_status tvcut_batch_cut(tvcut_batch_t b, int g, uint8_t* labels, int space,
 /* Product-space state of grid g (2 x H_g x W_g values of the iterate type). */
 tvcut_status tvcut_batch_get_state(tvcut_batch_t b, int g, void* s, int space);
 
-/* Time the chain-prox launch for CTA sizes {64, 128, 256} and {4, 8, 16}
- * CTAs per SM on the current inputs and keep the fastest; chosen (may be
- * NULL) receives {threads, ctas_per_sm}.  Results do not depend on it. */
+/* Time the chain-prox launch for CTA sizes {64, 128, 256}, {4, 8, 16} CTAs
+ * per SM and the two forms of the scan step (with branches, or predicated so
+ * that the lanes of a warp share one instruction stream) on the current
+ * inputs and keep the fastest; chosen (may be NULL, else 3 ints) receives
+ * {threads, ctas_per_sm, predicated}.  Results do not depend on it. */
 tvcut_status tvcut_batch_autotune(tvcut_batch_t b, int* chosen);
 
 /* ---- Learned warm start -------------------------------------------------

@@ -79,7 +79,7 @@ struct BatchArgs {
     const T* best_level;      // per grid (labels pass)
 };
 
-template <typename T>
+template <typename T, bool PRED>
 __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
 {
     __shared__ int item_s;
@@ -93,12 +93,13 @@ __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
         for (int t = threadIdx.x; t < I.count; t += blockDim.x) {
             const GridDesc D = A.grids[I.g];
             const int c = I.c0 + t;
+            const int64_t b = D.off + c;
             if (I.axis == 0) {        // column c: H elements, stride W (natural)
-                const int64_t b = D.off + c;
-                scan_chain<T>(D.H, A.s0 + b, A.a0 + D.aoff0 + c, A.x0 + b, D.W);
+                if (PRED) scan_chain_predicated<T>(D.H, A.s0 + b, A.a0 + D.aoff0 + c, A.x0 + b, D.W);
+                else scan_chain<T>(D.H, A.s0 + b, A.a0 + D.aoff0 + c, A.x0 + b, D.W);
             } else {                  // row c: W elements, stride H (transposed)
-                const int64_t b = D.off + c;
-                scan_chain<T>(D.W, A.s1 + b, A.a1 + D.aoff1 + c, A.x1 + b, D.H);
+                if (PRED) scan_chain_predicated<T>(D.W, A.s1 + b, A.a1 + D.aoff1 + c, A.x1 + b, D.H);
+                else scan_chain<T>(D.W, A.s1 + b, A.a1 + D.aoff1 + c, A.x1 + b, D.H);
             }
         }
     }
@@ -365,6 +366,7 @@ struct tvcut_batch_ctx {
     // launch configuration (autotuned)
     int scan_threads = 128;
     int scan_ctas_per_sm = 8;
+    int scan_predicated = 1;          // step variant of the chain scan
     int sms = 152;
     // graph cache
     cudaGraphExec_t graph = nullptr;
@@ -698,7 +700,8 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
         A.check = it == iters - 1;
         cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
         if (e != cudaSuccess) return e;
-        batch_scan_kernel<T><<<b->sms * b->scan_ctas_per_sm, b->scan_threads, 0, b->stream>>>(A);
+        if (b->scan_predicated) batch_scan_kernel<T, true><<<b->sms * b->scan_ctas_per_sm, b->scan_threads, 0, b->stream>>>(A);
+        else batch_scan_kernel<T, false><<<b->sms * b->scan_ctas_per_sm, b->scan_threads, 0, b->stream>>>(A);
         if (aar) batch_update_kernel<T, UPD_AAR><<<b->sms * 16, 256, 0, b->stream>>>(A);
         else batch_update_kernel<T, UPD_AP><<<b->sms * 16, 256, 0, b->stream>>>(A);
         e = cudaGetLastError();
@@ -887,34 +890,39 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
     const int threads[] = {64, 128, 256};
     const int per_sm[] = {4, 8, 16};
     float best = 1e30f;
-    int bt = b->scan_threads, bp = b->scan_ctas_per_sm;
-    for (int t : threads)
-        for (int q : per_sm) {
-            float tot = 0.f;
-            for (int rep = 0; rep < 3; ++rep) {
-                BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream), "autotune");
-                BCK(b, cudaEventRecord(e0, b->stream), "autotune");
-                batch_scan_kernel<T><<<b->sms * q, t, 0, b->stream>>>(A);
-                BCK(b, cudaGetLastError(), "autotune");
-                BCK(b, cudaEventRecord(e1, b->stream), "autotune");
-                BCK(b, cudaEventSynchronize(e1), "autotune");
-                float ms = 0.f;
-                BCK(b, cudaEventElapsedTime(&ms, e0, e1), "autotune");
-                if (rep > 0) tot += ms;
+    int bt = b->scan_threads, bp = b->scan_ctas_per_sm, bv = b->scan_predicated;
+    for (int pv = 0; pv < 2; ++pv)
+        for (int t : threads)
+            for (int q : per_sm) {
+                float tot = 0.f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream), "autotune");
+                    BCK(b, cudaEventRecord(e0, b->stream), "autotune");
+                    if (pv) batch_scan_kernel<T, true><<<b->sms * q, t, 0, b->stream>>>(A);
+                    else batch_scan_kernel<T, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    BCK(b, cudaGetLastError(), "autotune");
+                    BCK(b, cudaEventRecord(e1, b->stream), "autotune");
+                    BCK(b, cudaEventSynchronize(e1), "autotune");
+                    float ms = 0.f;
+                    BCK(b, cudaEventElapsedTime(&ms, e0, e1), "autotune");
+                    if (rep > 0) tot += ms;
+                }
+                if (tot < best) {
+                    best = tot;
+                    bt = t;
+                    bp = q;
+                    bv = pv;
+                }
             }
-            if (tot < best) {
-                best = tot;
-                bt = t;
-                bp = q;
-            }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->scan_threads = bt;
     b->scan_ctas_per_sm = bp;
+    b->scan_predicated = bv;
     if (chosen) {
         chosen[0] = bt;
         chosen[1] = bp;
+        chosen[2] = bv;
     }
     return TVCUT_OK;
 }

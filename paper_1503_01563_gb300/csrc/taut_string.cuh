@@ -15,13 +15,24 @@ namespace tvcut {
 // that last limited the violated bound (the string bends there) and the scan
 // resumes after it.  Pointers advance by `stride` per element; only a rescan
 // recomputes them.
+// num / len for the segment updates of every scan kernel (all of them use
+// this one helper, so the thread and warp scans agree bit for bit): exact
+// division in FP64; in FP32 a product with one approximate reciprocal
+// instruction (relative error below 2^-22).
 template <typename T>
 __device__ __forceinline__ T div_len(T num, int len)
 {
-    if constexpr (sizeof(T) == 4) return num * __frcp_rn((float)len);   // 1/len correctly rounded
-    else return num / (T)len;
+    if constexpr (sizeof(T) == 4) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"((float)len));
+        return num * r;
+    } else {
+        return num / (T)len;
+    }
 }
 
+// The step with branches: lanes that bend, clamp or start a segment take
+// different paths.  Identical arithmetic to scan_chain_predicated below.
 template <typename T>
 __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const T* __restrict__ a,
                                            T* __restrict__ x, int64_t stride)
@@ -77,6 +88,66 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
             ih = il = i;
             ah = al = Ai;
         }
+        if (i == m - 1) {
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
+            break;
+        }
+        ++i;
+        pv += stride;
+        pa += stride;
+    }
+}
+
+// The per-element step is written without branches except two rare ones
+// (writing a finished segment and restarting behind the current element), so
+// that the lanes of a warp, which bend, clamp and restart at different
+// elements, stay on one instruction stream: every candidate update is
+// computed and the valid one selected.
+template <typename T>
+__device__ __forceinline__ void scan_chain_predicated(int m, const T* __restrict__ v, const T* __restrict__ a,
+                                           T* __restrict__ x, int64_t stride)
+{
+    int s = 0, i = 0, ih = 0, il = 0;
+    T u0 = T(0), th = T(0), tl = T(0), uh = T(0), ul = T(0), ah = T(0), al = T(0);
+    const T* pv = v;
+    const T* pa = a;
+    T* px = x;                                   // next element to write
+    for (;;) {
+        const T vi = *pv;
+        const T Ai = (i < m - 1) ? *pa : T(0);
+        const bool fresh = (i == s);             // first element of a segment
+        const T uhn = uh + (th - vi);
+        const T uln = ul + (tl - vi);
+        const bool bhi = !fresh && uhn < -Ai;    // the string bends up at ih
+        const bool blo = !fresh && !bhi && uln > Ai;
+        const bool bend = bhi || blo;
+        if (bend) {
+            const int e = bhi ? ih : il;
+            const T t = bhi ? th : tl;
+            u0 = bhi ? ah : -al;
+            for (int j = s; j <= e; ++j, px += stride) *px = t;
+            s = e + 1;
+            if (s < i) {                         // rescan from the bend
+                i = s;
+                pv = v + (int64_t)s * stride;
+                pa = a + (int64_t)s * stride;
+                continue;
+            }
+        }
+        const bool start = fresh || bend;        // a segment starts at i
+        const int len = i - s + 1;
+        const bool ch = !start && uhn > Ai;      // the upper slope is cut at i
+        const bool cl = !start && uln < -Ai;     // the lower slope is cut at i
+        const T thc = ch ? th - div_len<T>(uhn - Ai, len) : th;
+        const T tlc = cl ? tl + div_len<T>(-Ai - uln, len) : tl;
+        th = start ? vi + Ai - u0 : thc;
+        tl = start ? vi - Ai - u0 : tlc;
+        uh = (start || ch) ? Ai : uhn;
+        ul = (start || cl) ? -Ai : uln;
+        ih = (start || ch) ? i : ih;
+        il = (start || cl) ? i : il;
+        ah = (start || ch) ? Ai : ah;
+        al = (start || cl) ? Ai : al;
         if (i == m - 1) {
             for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
             break;

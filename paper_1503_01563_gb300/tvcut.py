@@ -424,9 +424,9 @@ class Batch:
         return s
 
     def autotune(self):
-        ch = (ctypes.c_int * 2)()
+        ch = (ctypes.c_int * 3)()
         _bcheck(lib().tvcut_batch_autotune(self.h, ch), self.h)
-        return int(ch[0]), int(ch[1])
+        return int(ch[0]), int(ch[1]), int(ch[2])
 
 
 def _ucheck(code, u):

@@ -89,8 +89,8 @@ def test_batch_autotune_keeps_results(tv):
     b.reset()
     b.iterate(5)
     before = [b.state(g) for g in range(len(DIMS))]
-    threads, per_sm = b.autotune()
-    assert threads in (64, 128, 256) and per_sm in (4, 8, 16)
+    threads, per_sm, pred = b.autotune()
+    assert threads in (64, 128, 256) and per_sm in (4, 8, 16) and pred in (0, 1)
     b.reset()
     b.iterate(5)
     for g in range(len(DIMS)):
