@@ -180,6 +180,14 @@ tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int space);
 tvcut_status tvcut_get_state(tvcut_t h, void* s, int space);
 tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
 
+/* Shadow dual variables of the current state: y_k = Pi_{K_k}(s_k), the
+ * projection of each block's state onto its polytope (Sec. 4.2-4.3), ndim*n
+ * values of the iterate type in grid layout.  These are the y_i that Sec. 4.4
+ * reuses to warm-start a similar problem: tvcut_set_state(h2, y) starts h2
+ * from them.  (Reusing the state itself also carries its divergent part,
+ * which grows with the iteration count, Sec. 4.3.)  Errors: STATE, CUDA. */
+tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space);
+
 /* Warm start from a predicted primal xhat (n FP32 values): every block gets
  * s_k = (w - xhat)/ndim + tau * xhat.  (With tau = 0 the blocks split w - xhat
  * evenly; tau > 0 adds the drift that the AAR iterates acquire, Sec. 4.3.)

@@ -507,6 +507,7 @@ extern "C" tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvc
     if (e != cudaSuccess) {
         tvcut_status st = bcuda(nullptr, e, "tvcut_batch_create");
         tvcut_batch_destroy(b);
+        cudaGetLastError();            // clear the runtime's last error
         return st;
     }
     b->wmax.assign(G, 0.0);

@@ -434,7 +434,25 @@ cudaError_t launch_transpose(const T* in, T* out, int64_t R, int64_t W, cudaStre
     return cudaGetLastError();
 }
 
+// y = s - x over n values (the shadow duals of a block from its state and prox)
+template <typename T>
+__global__ void shadow_kernel(const T* __restrict__ s, const T* __restrict__ x, T* __restrict__ y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = s[i] - x[i];
+}
+
+template <typename T>
+cudaError_t launch_shadow(const T* s, const T* x, T* y, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    shadow_kernel<T><<<blocks, 256, 0, st>>>(s, x, y, n);
+    return cudaGetLastError();
+}
+
 #define TVCUT_SCAN_INST(T)                                                                  \
+    template cudaError_t launch_shadow<T>(const T*, const T*, T*, int64_t, cudaStream_t);   \
     template cudaError_t launch_scan<T>(ScanArgs<T>, cudaStream_t);                         \
     template cudaError_t launch_update<T>(int, const UpdateArgs<T>&, cudaStream_t);         \
     template cudaError_t launch_transpose<T>(const T*, T*, int64_t, int64_t, cudaStream_t);

@@ -179,6 +179,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     if (e != cudaSuccess) {
         tvcut_status st = cuda_fail(nullptr, e, "tvcut_create: allocation");
         tvcut_destroy(h);
+        cudaGetLastError();            // clear the runtime's last error: later calls must not see it
         return st;
     }
     *out = h;
@@ -646,6 +647,52 @@ extern "C" tvcut_status tvcut_get_state(tvcut_t h, void* s, int space)
     if (!s) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: NULL output");
     if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_state: bad space");
     return DISPATCH(h, get_state_impl, h, s, space);
+}
+
+// Shadow duals y_k = Pi_{K_k}(s_k) = s_k - prox(s_k) of the current state,
+// every block through the scan launch, out in grid layout.
+template <typename T>
+static tvcut_status get_dual_impl(tvcut_t h, void* out, int space)
+{
+    const int r = h->ndim;
+    ScanArgs<T> S;
+    memset(&S, 0, sizeof(S));
+    S.naxes = r;
+    for (int k = 0; k < r; ++k) {
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        S.ax[k].nchains = g.nchains;
+        S.ax[k].inner = g.inner;
+        S.ax[k].m = g.m;
+        S.ax[k].transposed = (h->tlast && k == r - 1) ? 1 : 0;
+        S.ax[k].v = S_of<T>(h, k);
+        S.ax[k].a = (const T*)h->a[k];
+        S.ax[k].x = XK_of<T>(h, k);
+    }
+    CK(h, traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); }), "tvcut_get_dual");
+    for (int k = 0; k < r; ++k)
+        CK(h, launch_shadow<T>(S_of<T>(h, k), XK_of<T>(h, k), XK_of<T>(h, k), h->n, h->stream), "tvcut_get_dual");
+    const cudaMemcpyKind kind = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int plain = h->tlast ? r - 1 : r;
+    CK(h, cudaMemcpyAsync(out, h->xk, sizeof(T) * (size_t)(plain * h->n), kind, h->stream), "tvcut_get_dual");
+    if (h->tlast) {
+        // the last block back to grid layout, through the P|x scratch (2n values)
+        T* tmp = P_of<T>(h);
+        CK(h, launch_transpose<T>(XK_of<T>(h, r - 1), tmp, cols_of(h), rows_of(h), h->stream), "tvcut_get_dual");
+        CK(h, cudaMemcpyAsync((T*)out + (int64_t)(r - 1) * h->n, tmp, sizeof(T) * (size_t)h->n, kind, h->stream),
+           "tvcut_get_dual");
+        h->x_valid = h->labels_valid = false;        // the scratch held the primal
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_dual");
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space)
+{
+    if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_get_dual: NULL handle");
+    if (!y) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: NULL output");
+    if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: bad space");
+    if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_get_dual: unary and all edge weights must be set first");
+    return DISPATCH(h, get_dual_impl, h, y, space);
 }
 
 template <typename T>

@@ -171,6 +171,8 @@ template <typename T>
 cudaError_t launch_update(int mode, const UpdateArgs<T>& args, cudaStream_t s);
 template <typename T>
 cudaError_t launch_transpose(const T* in, T* out, int64_t rows, int64_t cols, cudaStream_t s);
+template <typename T>
+cudaError_t launch_shadow(const T* s, const T* x, T* y, int64_t n, cudaStream_t st);
 
 ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
 

@@ -377,6 +377,7 @@ extern "C" tvcut_status tvcut_unet_create(int base, int N, int H, int W, uint64_
     if (e == cudaSuccess) e = cudaMemset(u->v, 0, pb);
     if (e != cudaSuccess) {
         tvcut_unet_destroy(u);
+        cudaGetLastError();            // clear the runtime's last error
         return ufail(nullptr, TVCUT_ERR_OOM, "tvcut_unet_create: allocation");
     }
     // He-normal weights (Box-Muller on splitmix64), zero biases
@@ -396,6 +397,7 @@ extern "C" tvcut_status tvcut_unet_create(int base, int N, int H, int W, uint64_
     if (st != TVCUT_OK) {
         std::string m = u->err;
         tvcut_unet_destroy(u);
+        cudaGetLastError();
         return ufail(nullptr, st, m.empty() ? "tvcut_unet_create failed" : m);
     }
     *out = u;

@@ -27,7 +27,7 @@ EXPORTED = [
     "tvcut_default_params", "tvcut_create", "tvcut_destroy", "tvcut_last_error",
     "tvcut_set_unary", "tvcut_set_weights", "tvcut_reset", "tvcut_iterate", "tvcut_cut",
     "tvcut_get_primal", "tvcut_get_state", "tvcut_set_state", "tvcut_warmstart_primal",
-    "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc",
+    "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc", "tvcut_get_dual",
     "tvcut_batch_create", "tvcut_batch_destroy", "tvcut_batch_last_error", "tvcut_batch_set_unary",
     "tvcut_batch_set_weights", "tvcut_batch_reset", "tvcut_batch_iterate", "tvcut_batch_cut",
     "tvcut_batch_get_state", "tvcut_batch_autotune",
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "tvcut_get_primal": (st, [P, P, c_int, c_int]),
         "tvcut_get_state": (st, [P, P, c_int]),
         "tvcut_set_state": (st, [P, P, c_int]),
+        "tvcut_get_dual": (st, [P, P, c_int]),
         "tvcut_warmstart_primal": (st, [P, P, ctypes.c_float, c_int]),
         "tvcut_project_chains": (st, [c_int, P, c_int, P, P, P, c_int, c_int, P]),
         "tvcut_profile": (st, [P, c_int]),
@@ -353,6 +354,12 @@ class Solver:
         s = np.empty((len(self.dims),) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
         tvcut_get_state(self.h, s)
         return s
+
+    def dual(self):
+        """Shadow duals y_k of the current state, shape (ndim,) + dims."""
+        y = np.empty((len(self.dims),) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
+        _check(lib().tvcut_get_dual(self.h, ctypes.c_void_p(y.ctypes.data), HOST), self.h)
+        return y
 
     def set_state(self, s):
         want = np.float64 if self.dtype == F64 else np.float32
