@@ -57,13 +57,21 @@ def make_problem(name):
     return inputs.segmentation_problem(wl["dims"], wl["seed"])
 
 
-def kernel_bytes_per_vertex(ndim):
+def kernel_bytes_per_vertex(ndim, algo="aar"):
     """Algorithmic bytes per vertex of one launch of each kernel kind (FP32
     state and weights; compact weights have dims[k]-1 entries per chain,
-    counted as one per vertex).  prox (the scan launch, all blocks): read s_k
-    and a_k, write x_k, for every block.  update: read w, every s_k and x_k,
-    write every s_k.  A check iteration's update also writes the primal (+4 B).
-    """
+    counted as one per vertex).
+
+    AAR and AP: prox (the scan launch, all blocks) reads s_k and a_k and
+    writes x_k for every block; update reads w, every s_k and x_k and writes
+    every s_k.  A check iteration's update also writes the primal (+4 B).
+
+    BCD (one block per launch): prox (the scan in projection mode) reads v_k
+    and a_k and writes y_k; update (forming v_k = w - sum_{j != k} y_j) reads
+    w and ndim-1 duals and writes v_k.  A check iteration adds one update that
+    reads all ndim duals (+4 B)."""
+    if algo == "bcd":
+        return {"prox": 12, "update": 4 * ndim + 4}
     return {"prox": 12 * ndim, "update": 4 + 12 * ndim}
 
 
@@ -138,10 +146,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_leg(name, w, a, budget_s=12.0):
-    """Oracle (FP64 AAR with its taut-string prox, OpenMP over chains) on the
-    host cores, timed on a bounded sample: whole-grid iterations until the
-    time budget is spent; plus the oracle's exact min-cut value E*."""
+ALGOS = {"aar": 0, "ap": 1, "bcd": 2}
+
+
+def cpu_leg(name, w, a, budget_s=12.0, algo="aar"):
+    """Oracle (FP64, the same algorithm, its taut-string prox with OpenMP over
+    chains) on the host cores, timed on a bounded sample: whole-grid
+    iterations until the time budget is spent; plus the oracle's exact
+    min-cut value E*."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -149,16 +161,17 @@ def cpu_leg(name, w, a, budget_s=12.0):
     e_star = oracle.maxflow(w, a, 1)[1]
     t_mf = time.perf_counter() - t0
     n = int(np.prod(w.shape))
-    s = oracle.cold_state(oracle.AAR, w)
+    code = ALGOS[algo]
+    s = oracle.cold_state(code, w)
     iters, t_it = 0, 0.0
     while t_it < budget_s and iters < 200:
         t0 = time.perf_counter()
-        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
         t_it += time.perf_counter() - t0
         iters += 1
     value = n * iters / t_it / 1e6
     return e_star, {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                    "sample": f"{iters} FP64 AAR iterations over the full {name} grid ({t_it:.1f} s), "
+                    "sample": f"{iters} FP64 {algo.upper()} iterations over the full {name} grid ({t_it:.1f} s), "
                               f"OpenMP over chains; max-flow E* took {t_mf:.1f} s"}
 
 
@@ -171,12 +184,13 @@ def run_reference(args):
     w, a = make_problem(args.workload)
     n = int(np.prod(w.shape))
     cores = os.cpu_count() or 1
-    s = oracle.cold_state(oracle.AAR, w)
+    code = ALGOS[args.algo]
+    s = oracle.cold_state(code, w)
     for _ in range(args.warmup):
-        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, _ = oracle.iterate(oracle.AAR, w, a, s, 1, nthreads=cores)
+        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt / 1e6
     out = {"impl": "reference", "metric": "Mvertex-iter/s", "value": value, "unit": "Mvertex-iter/s",
@@ -184,9 +198,10 @@ def run_reference(args):
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "dims": list(WORKLOADS[args.workload].get("dims", ())),
-                      "algo": "AAR", "step": "one whole-grid AAR iteration of the CPU oracle"},
+                      "algo": args.algo.upper(),
+                      "step": f"one whole-grid {args.algo.upper()} iteration of the CPU oracle"},
            "cpu_baseline": {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{args.steps} whole-grid FP64 AAR iterations"},
+                            "sample": f"{args.steps} whole-grid FP64 {args.algo.upper()} iterations"},
            "e2e": {"value": value, "unit": "Mvertex-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -478,11 +493,12 @@ def run_ours(args):
     dims = tuple(w.shape)
     n = int(np.prod(dims))
     ndim = len(dims)
+    algo = ALGOS[args.algo]
 
     # CPU leg (rank 0): oracle E* and the oracle's own throughput
     e_star, cpu_base = None, None
     if rank == 0:
-        e_star, cpu_base = cpu_leg(args.workload, w, a, budget_s=args.cpu_budget)
+        e_star, cpu_base = cpu_leg(args.workload, w, a, budget_s=args.cpu_budget, algo=args.algo)
 
     stream = torch.cuda.current_stream(dev)
     wd = torch.from_numpy(w).to(dev)
@@ -492,7 +508,7 @@ def run_ours(args):
     kstar = None
     cap = WORKLOADS[args.workload]["cap"]
     if rank == 0:
-        probe = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+        probe = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
         probe.set_problem(wd, ad)
         for k in range(1, cap + 1):
             _, st = probe.iterate(1)
@@ -506,7 +522,7 @@ def run_ours(args):
         dist.broadcast(t, 0)
         iters = int(t.item())
 
-    solver = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
     solver.set_problem(wd, ad)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -547,7 +563,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest device-time share)
     kinds = ["prox", "update", "check", "other"]
-    bpv = kernel_bytes_per_vertex(ndim)
+    bpv = kernel_bytes_per_vertex(ndim, args.algo)
     dom = max(range(2), key=lambda k: kms[k])
     dom_name = kinds[dom]
     launches = int(klaunch[dom])
@@ -557,16 +573,16 @@ def run_ours(args):
     avg_s = kms[dom] / 1e3 / max(launches, 1)
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_kind = peaks()
-    traffic = kernel_traffic(dom_name, args.workload)
-    iter_bytes = (bpv["prox"] + bpv["update"]) * n
+    traffic = kernel_traffic(dom_name, args.workload if args.algo == "aar" else f"{args.workload}:{args.algo}")
+    moved = (bpv["prox"] * klaunch[0] + bpv["update"] * klaunch[1] + 4 * args.steps) * n
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
                 "share_of_step": float(kms[dom] / max(kms.sum(), 1e-9)),
-                "iteration_GBps": float(iter_bytes * klaunch[0] / max((kms[0] + kms[1]) / 1e3, 1e-12) / 1e9)}
+                "iteration_GBps": float(moved / max((kms[0] + kms[1]) / 1e3, 1e-12) / 1e9)}
 
     # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
-    e2e_solver = tvcut.Solver(dims, algo=tvcut.AAR, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    e2e_solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
     labels = np.empty(dims, dtype=np.uint8)
     w_pin = torch.from_numpy(w).pin_memory()
     a_pin = [torch.from_numpy(x).pin_memory() for x in a]
@@ -591,7 +607,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "dims": list(dims), "algo": "AAR", "iterate": "f32",
+            "config": {"workload": args.workload, "dims": list(dims), "algo": args.algo.upper(), "iterate": "f32",
                        "iters_per_step": iters, "step": "cold start + iterations to the oracle-equal cut + cut",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB buffer written between steps"},
@@ -622,6 +638,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="volume256")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--algo", choices=sorted(ALGOS), default="aar",
+                    help="iteration of the volume256/seg1024 workloads: AAR (Eq. 3), AP (Sec. 4.2), BCD (Sec. 4.1)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -62,10 +62,13 @@ typedef enum {
 
 enum { TVCUT_I32 = 0, TVCUT_F32 = 1, TVCUT_F64 = 2 };    /* element types */
 enum { TVCUT_HOST = 0, TVCUT_DEVICE = 1 };                /* pointer space */
-enum { TVCUT_AAR = 0, TVCUT_AP = 1 };                     /* algorithms    */
+enum { TVCUT_AAR = 0, TVCUT_AP = 1, TVCUT_BCD = 2 };      /* algorithms    */
 
 typedef struct {
-    int algo;            /* TVCUT_AAR (Eq. 3, default) or TVCUT_AP (Sec. 4.2) */
+    int algo;            /* TVCUT_AAR (Eq. 3, default), TVCUT_AP (Sec. 4.2) or
+                            TVCUT_BCD (Sec. 4.1, cyclic projections: blocks in
+                            turn, y_k <- Pi_{K_k}(w - sum_{j != k} y_j); state y,
+                            cold start 0) */
     int iterate_dtype;   /* TVCUT_F32 (default) or TVCUT_F64: precision of the
                             state and of the chain prox; gaps and energies are
                             always accumulated in FP64 (and int64 for exact
@@ -152,7 +155,8 @@ tvcut_status tvcut_set_weights(tvcut_t h, int axis, const void* a, int dtype,
                                int space);
 
 /* Cold start: AAR z = 0, AP lambda_k = w / ndim (the projection of 0 onto the
- * consensus set L of Eq. dualdec).  Errors: STATE (no unary yet), CUDA. */
+ * consensus set L of Eq. dualdec), BCD y = 0.  Errors: STATE (no unary yet),
+ * CUDA. */
 tvcut_status tvcut_reset(tvcut_t h);
 
 /* Run up to max_iters iterations (max_iters >= 1).  Every check_every
@@ -175,7 +179,7 @@ tvcut_status tvcut_cut(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out);
 tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int space);
 
 /* Copy the product-space state (ndim*n values of the iterate type: z for AAR,
- * lambda for AP) out of / into the handle: checkpoint, resume, and the warm
+ * lambda for AP, the block duals y for BCD) out of / into the handle: checkpoint, resume, and the warm
  * start of Sec. 4.4 (reuse the state of a similar, earlier problem). */
 tvcut_status tvcut_get_state(tvcut_t h, void* s, int space);
 tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
@@ -185,7 +189,8 @@ tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
  * values of the iterate type in grid layout.  These are the y_i that Sec. 4.4
  * reuses to warm-start a similar problem: tvcut_set_state(h2, y) starts h2
  * from them.  (Reusing the state itself also carries its divergent part,
- * which grows with the iteration count, Sec. 4.3.)  Errors: STATE, CUDA. */
+ * which grows with the iteration count, Sec. 4.3.)  For TVCUT_BCD the state
+ * is already y and this copies it.  Errors: STATE, CUDA. */
 tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space);
 
 /* Warm start from a predicted primal xhat (n FP32 values): every block gets

@@ -40,7 +40,7 @@ __device__ __forceinline__ void scan_cp_wait()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <typename T>
+template <typename T, bool SHADOW>
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
 {
     int k = 0;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
         abase = o * (int64_t)(X.m - 1) * X.inner + q;
         stride = X.inner;
     }
-    scan_chain<T>(X.m, X.v + base, X.a + abase, X.x + base, stride);
+    scan_chain<T, SHADOW>(X.m, X.v + base, X.a + abase, X.x + base, stride);
 }
 
 // ---- warp-per-chain speculative scan ------------------------------------------
@@ -155,7 +155,7 @@ __device__ __forceinline__ int lane_scan(LaneState<T>& st, int m, int stop, cons
 
 constexpr int kWarpChains = 8;      // chains (warps) per CTA of the warp scan
 
-template <typename T>
+template <typename T, bool SHADOW>
 __global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, int nc)
 {
     extern __shared__ __align__(16) unsigned char wsm[];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, 
     const bool active = lane < npieces;
     const bool lastp = lane == npieces - 1;
     auto write_seg = [&](int from, int to, T t) {
-        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = t;
+        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = SHADOW ? cv[skew32(j)] - t : t;
     };
 
     // phase 1: every piece from a guessed state
@@ -260,14 +260,17 @@ template <typename T>
 cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
 {
     // one thread per chain unless the launch has too few chains to fill the
-    // GPU, in which case long chains go to the warp-per-chain scan
+    // GPU, in which case long chains go to the warp-per-chain scan (measured
+    // on 256^3: 65,536 chains of 256 run faster as warps, 196,608 as threads)
     int64_t total = 0;
     for (int k = 0; k < A.naxes; ++k) total += A.ax[k].nchains;
     ScanArgs<T> thr, wrp;
     thr.naxes = wrp.naxes = 0;
+    thr.force = wrp.force = A.force;
+    thr.shadow = wrp.shadow = A.shadow;
     for (int k = 0; k < A.naxes; ++k) {
         const ScanAxis<T>& X = A.ax[k];
-        bool warp = X.m >= 64 && total < 32768 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        bool warp = X.m >= 64 && total <= 98304 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
         if (A.force == 1) warp = false;
         if (A.force == 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
         if (warp) wrp.ax[wrp.naxes++] = X;
@@ -280,7 +283,8 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
             blocks += (thr.ax[k].nchains + kScanThreads - 1) / kScanThreads;
         }
         if (blocks > 0) {
-            scan_kernel<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
+            if (A.shadow) scan_kernel<T, true><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
+            else scan_kernel<T, false><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -301,12 +305,15 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-            e = cudaFuncSetAttribute(wscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            e = cudaFuncSetAttribute(wscan_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(wscan_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) attr_set[dev] = true;
         }
         if (blocks > 0) {
-            wscan_kernel<T><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
+            if (A.shadow) wscan_kernel<T, true><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
+            else wscan_kernel<T, false><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
             return cudaGetLastError();
         }
     }
@@ -434,25 +441,65 @@ cudaError_t launch_transpose(const T* in, T* out, int64_t R, int64_t W, cudaStre
     return cudaGetLastError();
 }
 
-// y = s - x over n values (the shadow duals of a block from its state and prox)
-template <typename T>
-__global__ void shadow_kernel(const T* __restrict__ s, const T* __restrict__ x, T* __restrict__ y, int64_t n)
+// BCD (Sec. 4.1): out = w - sum_{j != skip} y_j for every vertex, written in
+// the layout of block `skip` (transposed when skip is the last block; natural
+// when skip < 0 or another block).  Tile-based like the update: the last
+// block's duals are transposed through shared memory.
+template <typename T, int R_>
+__global__ void __launch_bounds__(kUpdThreads) bcd_prepare_kernel(UpdateArgs<T> A, int skip)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = s[i] - x[i];
+    __shared__ T sy[kTile][kTile + 1];
+    const int64_t R = A.rows, W = A.cols;
+    const int64_t tiles_c = (W + kTile - 1) / kTile;
+    const int64_t r0 = (blockIdx.x / tiles_c) * kTile;
+    const int64_t c0 = (blockIdx.x % tiles_c) * kTile;
+    constexpr int last = R_ - 1;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+    if (skip != last) {
+#pragma unroll
+        for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+            const int64_t c = c0 + cc, r = r0 + tx;
+            if (c < W && r < R) sy[cc][tx] = A.s[last][c * R + r];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTile; rr += kUpdThreads / kTile) {
+        const int64_t r = r0 + rr, c = c0 + tx;
+        if (r >= R || c >= W) continue;
+        const int64_t g = r * W + c;
+        T v = A.w[g];
+#pragma unroll
+        for (int k = 0; k < R_; ++k) {
+            if (k == skip) continue;
+            v -= (k == last) ? sy[tx][rr] : A.s[k][g];
+        }
+        if (skip == last) sy[tx][rr] = v;
+        else A.xout[g] = v;
+    }
+    if (skip == last) {
+        __syncthreads();
+#pragma unroll
+        for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+            const int64_t c = c0 + cc, r = r0 + tx;
+            if (c < W && r < R) A.xout[c * R + r] = sy[cc][tx];
+        }
+    }
 }
 
 template <typename T>
-cudaError_t launch_shadow(const T* s, const T* x, T* y, int64_t n, cudaStream_t st)
+cudaError_t launch_bcd_prepare(const UpdateArgs<T>& A, int skip, cudaStream_t s)
 {
-    if (n <= 0) return cudaSuccess;
-    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    shadow_kernel<T><<<blocks, 256, 0, st>>>(s, x, y, n);
+    const int64_t tiles = ((A.rows + kTile - 1) / kTile) * ((A.cols + kTile - 1) / kTile);
+    if (tiles == 0) return cudaSuccess;
+    if (A.r == 3) bcd_prepare_kernel<T, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A, skip);
+    else if (A.r == 2) bcd_prepare_kernel<T, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A, skip);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 #define TVCUT_SCAN_INST(T)                                                                  \
-    template cudaError_t launch_shadow<T>(const T*, const T*, T*, int64_t, cudaStream_t);   \
+    template cudaError_t launch_bcd_prepare<T>(const UpdateArgs<T>&, int, cudaStream_t);    \
     template cudaError_t launch_scan<T>(ScanArgs<T>, cudaStream_t);                         \
     template cudaError_t launch_update<T>(int, const UpdateArgs<T>&, cudaStream_t);         \
     template cudaError_t launch_transpose<T>(const T*, T*, int64_t, int64_t, cudaStream_t);

@@ -33,7 +33,10 @@ __device__ __forceinline__ T div_len(T num, int len)
 
 // The step with branches: lanes that bend, clamp or start a segment take
 // different paths.  Identical arithmetic to scan_chain_predicated below.
-template <typename T>
+//
+// SHADOW: write v_j - t (the projection of v onto the block's polytope,
+// Sec. 3.1) instead of the prox value t; x must not alias v then.
+template <typename T, bool SHADOW = false>
 __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const T* __restrict__ a,
                                            T* __restrict__ x, int64_t stride)
 {
@@ -55,7 +58,7 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
                 const int e = bhi ? ih : il;
                 const T t = bhi ? th : tl;
                 u0 = bhi ? ah : -al;
-                for (int j = s; j <= e; ++j, px += stride) *px = t;
+                for (int j = s; j <= e; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - t : t;
                 s = e + 1;
                 if (s < i) {                         // rescan from the bend
                     i = s;
@@ -89,7 +92,7 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
             ah = al = Ai;
         }
         if (i == m - 1) {
-            for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - th : th;
             break;
         }
         ++i;

@@ -121,7 +121,8 @@ extern "C" void tvcut_destroy(tvcut_t h)
 
 static bool valid_params(const tvcut_params* p, std::string& why)
 {
-    if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP) { why = "params.algo must be TVCUT_AAR or TVCUT_AP"; return false; }
+    if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP && p->algo != TVCUT_BCD) { why = "params.algo must be TVCUT_AAR, TVCUT_AP or TVCUT_BCD"; return false; }
+    if (p->algo == TVCUT_BCD && p->mapping >= 1 && p->mapping <= 4) { why = "TVCUT_BCD runs on the scan schedule (mapping -1, 0, 5 or 6)"; return false; }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
     if (p->mapping < -1 || p->mapping > 6) { why = "params.mapping must be -1 (auto) or 0..6"; return false; }
@@ -348,9 +349,64 @@ static cudaError_t run_sweeps(tvcut_t h, int first, int mid, int last, int check
 // One iteration (or, with mode UPD_EVAL, only the primal of the current
 // state).  Scan schedule: one scan launch for all blocks + one update launch;
 // fused schedule (mapping 1..4): one sweep per block, the last one updating.
+// One cycle of block coordinate descent (Sec. 4.1, cyclic projections): for
+// k = 0..r-1, v = w - sum_{j != k} y_j, y_k = v - prox_{f_k}(v).  The state
+// holds the y_k; on check iterations the primal w - sum_k y_k goes to x.
+template <typename T>
+static cudaError_t run_bcd(tvcut_t h, int check)
+{
+    const int r = h->ndim;
+    UpdateArgs<T> U;
+    memset(&U, 0, sizeof(U));
+    U.rows = rows_of(h);
+    U.cols = cols_of(h);
+    U.r = r;
+    for (int k = 0; k < r; ++k) U.s[k] = S_of<T>(h, k);
+    U.w = (const T*)h->w;
+    U.xout = P_of<T>(h);                                  // v_k, in block k's layout
+    for (int k = 0; k < r; ++k) {
+        cudaError_t e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, k, h->stream); });
+        if (e != cudaSuccess) return e;
+        ScanArgs<T> S;
+        memset(&S, 0, sizeof(S));
+        S.naxes = 1;
+        S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        S.ax[0].nchains = g.nchains;
+        S.ax[0].inner = g.inner;
+        S.ax[0].m = g.m;
+        S.ax[0].transposed = k == r - 1 ? 1 : 0;
+        S.ax[0].v = P_of<T>(h);
+        S.ax[0].a = (const T*)h->a[k];
+        S.ax[0].x = S_of<T>(h, k);
+        S.shadow = 1;                                     // y_k = v_k - prox(v_k)
+        e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
+        if (e != cudaSuccess) return e;
+    }
+    if (check) {
+        U.xout = X_of<T>(h);
+        return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t run_iteration(tvcut_t h, int mode, int check)
 {
+    if (h->p.algo == TVCUT_BCD) {
+        if (mode == UPD_EVAL) {           // primal of the current duals
+            UpdateArgs<T> U;
+            memset(&U, 0, sizeof(U));
+            U.rows = rows_of(h);
+            U.cols = cols_of(h);
+            U.r = h->ndim;
+            for (int k = 0; k < h->ndim; ++k) U.s[k] = S_of<T>(h, k);
+            U.w = (const T*)h->w;
+            U.xout = X_of<T>(h);
+            return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
+        }
+        return run_bcd<T>(h, check);
+    }
     if (!h->tlast) {
         if (mode == UPD_EVAL) return run_sweeps<T>(h, MODE_EVAL_FIRST, MODE_EVAL_MID, MODE_EVAL_LAST, 1);
         if (mode == UPD_AAR) return run_sweeps<T>(h, MODE_AAR_FIRST, MODE_AAR_MID, MODE_AAR_LAST, check);
@@ -668,9 +724,8 @@ static tvcut_status get_dual_impl(tvcut_t h, void* out, int space)
         S.ax[k].a = (const T*)h->a[k];
         S.ax[k].x = XK_of<T>(h, k);
     }
+    S.shadow = 1;                                         // y_k = s_k - prox(s_k)
     CK(h, traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); }), "tvcut_get_dual");
-    for (int k = 0; k < r; ++k)
-        CK(h, launch_shadow<T>(S_of<T>(h, k), XK_of<T>(h, k), XK_of<T>(h, k), h->n, h->stream), "tvcut_get_dual");
     const cudaMemcpyKind kind = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const int plain = h->tlast ? r - 1 : r;
     CK(h, cudaMemcpyAsync(out, h->xk, sizeof(T) * (size_t)(plain * h->n), kind, h->stream), "tvcut_get_dual");
@@ -692,6 +747,7 @@ extern "C" tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space)
     if (!y) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: NULL output");
     if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: bad space");
     if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_get_dual: unary and all edge weights must be set first");
+    if (h->p.algo == TVCUT_BCD) return DISPATCH(h, get_state_impl, h, y, space);   // the BCD state is y itself
     return DISPATCH(h, get_dual_impl, h, y, space);
 }
 

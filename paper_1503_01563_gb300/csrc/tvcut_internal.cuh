@@ -39,6 +39,7 @@ template <typename T>
 struct ScanArgs {
     int naxes;
     int force;             // 0 automatic, 1 thread per chain, 2 warp per chain
+    int shadow;            // 1: write v - prox(v) (the projection onto K_k) instead of prox(v)
     ScanAxis<T> ax[3];
 };
 
@@ -172,7 +173,7 @@ cudaError_t launch_update(int mode, const UpdateArgs<T>& args, cudaStream_t s);
 template <typename T>
 cudaError_t launch_transpose(const T* in, T* out, int64_t rows, int64_t cols, cudaStream_t s);
 template <typename T>
-cudaError_t launch_shadow(const T* s, const T* x, T* y, int64_t n, cudaStream_t st);
+cudaError_t launch_bcd_prepare(const UpdateArgs<T>& args, int skip, cudaStream_t s);
 
 ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
 
