@@ -12,8 +12,8 @@ Minimization" they follow:
 - ``tv1d_certificate``  Lagrangian certificate of a chain prox (Sec. 3.2, 2.3)
 - ``project_block``     Pi_{K_k} = I - prox on every chain of one block
                         (Sec. 3.1, Sec. 4.2)
-- ``iterate``           AAR (Eq. 3), AP (Sec. 4.2), BCD (Sec. 4.1)
-- ``cold_state``        z = 0 (AAR), lambda = Pi_L(0) (AP), y = 0 (BCD)
+- ``iterate``           AAR (Eq. 3), AP (Sec. 4.2), BCD and FISTA (Sec. 4.1)
+- ``cold_state``        z = 0 (AAR), lambda = Pi_L(0) (AP), y = 0 (BCD, FISTA)
 - ``tv_value``          f(x) = sum_e a_e |x_i - x_j| (Eq. 2)
 - ``energy``            E(l) = f(l) - w^T l (problem (D))
 - ``bruteforce``        min over all 2^n labellings (problem (D))
@@ -37,7 +37,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SOURCES = ["tv1d.c", "dr.c", "maxflow.c"]
 _lib = None
 
-AAR, AP, BCD = 0, 1, 2
+AAR, AP, BCD, FISTA = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -152,7 +152,8 @@ def cold_state(algo: int, w) -> np.ndarray:
 
 def iterate(algo: int, w, a, state, iters: int, nthreads: int = 1):
     """Run `iters` iterations; returns (new_state, x) with x = w - sum_k y_k
-    of the last shadow.  `state` has shape (ndim,) + grid shape."""
+    of the last shadow.  `state` has shape (ndim,) + grid shape.  FISTA's
+    momentum starts afresh at every call, so run it in one call."""
     w = _f64(w)
     dims, nd = _dims(w.shape)
     wt = _Weights(w.shape, a)

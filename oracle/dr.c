@@ -12,6 +12,14 @@
  *   AP     : y <- Pi_K(lambda), lambda <- Pi_L(y)           (Sec. 4.2).
  *   BCD    : y_k <- Pi_{K_k}(w - sum_{j != k} y_j), k = 0..r-1 in turn
  *            (Sec. 4.1, reading the printed inner sum over y_i as y_j).
+ *   FISTA  : accelerated projected gradient on the smooth dual
+ *            g(y) = 1/2 ||sum_k y_k - w||^2 over K_1 x ... x K_r (Sec. 4.1,
+ *            problem dualdec2).  grad_k g(u) = sum_j u_j - w for every block,
+ *            Lipschitz constant r, so the gradient step from u is
+ *            u - grad g(u) / r = Pi_L(u) and y <- Pi_K(Pi_L(u)); then
+ *            t+ = (1 + sqrt(1 + 4 t^2)) / 2 and u <- y + ((t - 1) / t+)(y - y_prev)
+ *            (Beck and Teboulle's FISTA with constant step; t = 1 and u = y
+ *            at the start of every call, so the momentum restarts per call).
  *   primal : x = w - sum_k y_k                      (Sec. 2.3, x = w - y).
  */
 #include "oracle.h"
@@ -115,7 +123,7 @@ int oracle_iterate(int algo, int ndim, const int64_t* dims, const double* w,
                    const double* const* a, double* s, int64_t iters,
                    double* x_out, int nthreads)
 {
-    if (ndim < 1 || ndim > 3 || iters < 0 || algo < 0 || algo > 2) return -1;
+    if (ndim < 1 || ndim > 3 || iters < 0 || algo < 0 || algo > 3) return -1;
     int64_t n = grid_size(ndim, dims);
     int r = ndim;
     double* y = (double*)malloc(sizeof(double) * (size_t)(r * n));
@@ -124,6 +132,11 @@ int oracle_iterate(int algo, int ndim, const int64_t* dims, const double* w,
     double* v = (double*)malloc(sizeof(double) * (size_t)n);
     if (!y || !t1 || !t2 || !v) { free(y); free(t1); free(t2); free(v); return -1; }
     int have_y = 0;
+    double tk = 1.0;                        /* FISTA: t_1 = 1, u_1 = y_prev = s */
+    if (algo == 3) {
+        memcpy(t2, s, sizeof(double) * (size_t)(r * n));      /* u      */
+        memcpy(y, s, sizeof(double) * (size_t)(r * n));       /* y_prev */
+    }
     for (int64_t it = 0; it < iters; ++it) {
         if (algo == 0) {
             /* AAR (Eq. 3): z <- 1/2 (R_L R_K z + z); shadow y = Pi_K(z). */
@@ -138,7 +151,7 @@ int oracle_iterate(int algo, int ndim, const int64_t* dims, const double* w,
             /* AP (Sec. 4.2): y = Pi_K(lambda); lambda = Pi_L(y). */
             project_K(ndim, dims, a, s, y, n, nthreads);
             project_L(r, n, w, y, s);
-        } else {
+        } else if (algo == 2) {
             /* BCD (Sec. 4.1): y_k <- Pi_{K_k}(w - sum_{j != k} y_j). */
             for (int k = 0; k < r; ++k) {
                 for (int64_t i = 0; i < n; ++i) {
@@ -150,12 +163,23 @@ int oracle_iterate(int algo, int ndim, const int64_t* dims, const double* w,
                 oracle_project_block(ndim, dims, k, v, a[k], s + k * n, nthreads);
             }
             memcpy(y, s, sizeof(double) * (size_t)(r * n));
+        } else {
+            /* FISTA: y = Pi_K(u - grad g(u) / r) = Pi_K(Pi_L(u)); momentum. */
+            project_L(r, n, w, t2, t1);
+            project_K(ndim, dims, a, t1, s, n, nthreads);
+            double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+            double beta = (tk - 1.0) / tn;
+            for (int64_t i = 0; i < r * n; ++i) {
+                t2[i] = s[i] + beta * (s[i] - y[i]);
+                y[i] = s[i];
+            }
+            tk = tn;
         }
         have_y = 1;
     }
     if (x_out) {
         if (!have_y) {
-            if (algo == 2) memcpy(y, s, sizeof(double) * (size_t)(r * n));
+            if (algo >= 2) memcpy(y, s, sizeof(double) * (size_t)(r * n));
             else project_K(ndim, dims, a, s, y, n, nthreads);
         }
         primal_from_y(r, n, w, y, x_out);

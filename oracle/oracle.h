@@ -52,7 +52,9 @@ void oracle_project_block(int ndim, const int64_t* dims, int axis,
 /* Run `iters` iterations of a product-space method (Sec. 4) from state `s`
  * (r*n doubles, updated in place).  algo 0: averaged alternating reflections
  * (Eq. 3, state z); 1: alternating projections (Sec. 4.2, state lambda);
- * 2: cyclic projections / block coordinate descent (Sec. 4.1, state y).
+ * 2: cyclic projections / block coordinate descent (Sec. 4.1, state y);
+ * 3: FISTA on the smooth dual of Sec. 4.1 (state y; the momentum starts
+ * afresh at every call: t = 1, extrapolated point = s).
  * a[k] points at axis k's compact weights.  x_out (n, may be NULL) receives
  * the primal x = w - sum_k y_k of the last shadow y computed (Eq. dualA and
  * the relation x = w - y of Sec. 2.3).  Returns 0, -1 on bad input. */
@@ -61,7 +63,7 @@ int oracle_iterate(int algo, int ndim, const int64_t* dims, const double* w,
                    double* x_out, int nthreads);
 
 /* Cold-start state of each method: AAR z = 0; AP lambda_k = w / r (the
- * projection of 0 onto L); BCD y = 0.  Writes r*n doubles. */
+ * projection of 0 onto L); BCD and FISTA y = 0.  Writes r*n doubles. */
 void oracle_cold_state(int algo, int ndim, const int64_t* dims,
                        const double* w, double* s);
 

@@ -1,16 +1,17 @@
 """Pins for the oracle's product-space methods (Sec. 4): AAR (Eq. 3), AP
-(Sec. 4.2) and BCD (Sec. 4.1).  Their limits are checked against a TV
+(Sec. 4.2), BCD and FISTA (Sec. 4.1).  Their limits are checked against a TV
 denoiser over all grid edges written here (dual projected gradient, no chain
 decomposition), against exact min-cuts (thresholding at zero, Sec. 2.3), and
 against properties the paper states or implies: dual feasibility, the duality
 gaps of Sec. 2.2-2.3, the divergence of the AAR iterates at the rate of the
-gap vector (Sec. 4.3), and monotone BCD."""
+gap vector (Sec. 4.3), monotone BCD, and for FISTA its reduction to AP while
+the momentum is zero and the O(1/k^2) bound of accelerated gradient methods."""
 import numpy as np
 import pytest
 
 from paper_1503_01563_gb300 import inputs
 
-AAR, AP, BCD = 0, 1, 2
+AAR, AP, BCD, FISTA = 0, 1, 2, 3
 
 
 def edges(dims, a):
@@ -63,7 +64,7 @@ def run(orc, algo, w, a, iters):
 def test_zero_weights_give_identity(orc):
     w, a = inputs.uniform_grid((5, 7), 2)
     a = [np.zeros_like(x) for x in a]
-    for algo in (AAR, AP, BCD):
+    for algo in (AAR, AP, BCD, FISTA):
         _, x = run(orc, algo, w, a, 1)
         np.testing.assert_allclose(x, w, atol=1e-12)
 
@@ -74,7 +75,7 @@ def test_separable_case(orc):
     w, a = inputs.uniform_grid((6, 9), 3)
     a = [np.zeros_like(a[0]), a[1]]
     want = np.stack([orc.tv1d_prox(w[h].astype(float), a[1][h].astype(float)) for h in range(6)])
-    for algo in (AAR, AP, BCD):
+    for algo in (AAR, AP, BCD, FISTA):
         _, x = run(orc, algo, w, a, 400)
         np.testing.assert_allclose(x, want, atol=1e-8)
 
@@ -83,7 +84,7 @@ def test_separable_case(orc):
 def test_limits_agree_with_graph_tv(orc, dims):
     w, a = inputs.uniform_grid(dims, 21, w_range=(-6, 6), a_range=(1, 3))
     ref = graph_tv_prox(w, a)
-    for algo in (AAR, AP, BCD):
+    for algo in (AAR, AP, BCD, FISTA):
         _, x = run(orc, algo, w, a, 3000)
         np.testing.assert_allclose(x, ref, atol=2e-6, err_msg=f"algo {algo}")
 
@@ -104,7 +105,7 @@ def test_threshold_gives_min_cut_bruteforce(orc):
 def test_threshold_gives_min_cut_maxflow(orc):
     w, a = inputs.uniform_grid((24, 20), 5)
     E, smin, smax = orc.min_cut(w, a)
-    for algo in (AAR, AP, BCD):
+    for algo in (AAR, AP, BCD, FISTA):
         _, x = run(orc, algo, w, a, 2500)
         assert orc.energy(w, a, (x > 1e-7).astype(np.uint8)) == E
         assert np.array_equal((x > 1e-7).astype(np.uint8), smin)
@@ -191,6 +192,50 @@ def test_cold_states(orc):
     w, _ = inputs.uniform_grid((3, 4, 5), 1)
     assert np.all(orc.cold_state(AAR, w) == 0)
     assert np.all(orc.cold_state(BCD, w) == 0)
+    assert np.all(orc.cold_state(FISTA, w) == 0)
     lam = orc.cold_state(AP, w)
     np.testing.assert_allclose(lam.sum(0), w)
     np.testing.assert_allclose(lam[0], lam[2])
+
+
+def test_fista_starts_as_ap(orc):
+    """FISTA's extrapolation weight (t_k - 1)/t_{k+1} is 0 for k = 1 (t_1 = 1),
+    so from y = 0 its first two iterates are projected gradient steps
+    y <- Pi_K(Pi_L(u)), which are AP's from lambda = Pi_L(0); the third
+    already differs (a dropped or misplaced momentum term fails here)."""
+    for dims in [(9, 11), (4, 5, 6)]:
+        w, a = inputs.uniform_grid(dims, 13)
+        for k in (1, 2):
+            _, xf = run(orc, FISTA, w, a, k)
+            _, xa = run(orc, AP, w, a, k)
+            np.testing.assert_allclose(xf, xa, atol=1e-12, err_msg=f"iterate {k}")
+        _, xf = run(orc, FISTA, w, a, 3)
+        _, xa = run(orc, AP, w, a, 3)
+        assert np.abs(xf - xa).max() > 1e-6
+
+
+def test_fista_rate_bound(orc):
+    """Beck and Teboulle's bound for FISTA with constant step 1/L:
+    g(y_k) - g* <= 2 L ||y_0 - y*||^2 / (k + 1)^2 for every minimiser y*, here
+    g(y) = 1/2 ||sum_k y_k - w||^2 = 1/2 ||x||^2, L = r (Sec. 4.1), y_0 = 0 and
+    y* the limit of cyclic projections."""
+    for dims in [(10, 12), (5, 4, 6)]:
+        w, a = inputs.uniform_grid(dims, 17)
+        r = len(dims)
+        ystar, xstar = run(orc, BCD, w, a, 4000)
+        gstar = 0.5 * np.sum(xstar ** 2)
+        D = np.sum(ystar ** 2)
+        for k in (1, 2, 3, 5, 8, 13, 21, 34, 55):
+            _, x = run(orc, FISTA, w, a, k)
+            assert 0.5 * np.sum(x ** 2) - gstar <= 2 * r * D / (k + 1) ** 2 + 1e-9, k
+
+
+def test_fista_faster_than_ap(orc):
+    """The momentum pays on these problems, as the paper's Table 1 reports
+    (FISTA needs fewer iterations than AP on every dataset listed)."""
+    w, a = inputs.uniform_grid((24, 20), 5)
+    _, xstar = run(orc, BCD, w, a, 4000)
+    gstar = 0.5 * np.sum(xstar ** 2)
+    _, xf = run(orc, FISTA, w, a, 150)
+    _, xa = run(orc, AP, w, a, 150)
+    assert 0.5 * np.sum(xf ** 2) - gstar < 0.1 * (0.5 * np.sum(xa ** 2) - gstar)
