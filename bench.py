@@ -64,15 +64,23 @@ def kernel_bytes_per_vertex(ndim, algo="aar"):
 
     AAR and AP: prox (the scan launch, all blocks) reads s_k and a_k and
     writes x_k for every block; update reads w, every s_k and x_k and writes
-    every s_k.  A check iteration's update also writes the primal (+4 B).
+    every s_k.  A checked iteration's update also writes the primal (+4 B).
 
     BCD (one block per launch): prox (the scan in projection mode) reads v_k
     and a_k and writes y_k; update (forming v_k = w - sum_{j != k} y_j) reads
-    w and ndim-1 duals and writes v_k.  A check iteration adds one update that
-    reads all ndim duals (+4 B)."""
+    w and ndim-1 duals and writes v_k.
+
+    FISTA: update (extrapolation and gradient step) reads w, every y_k and
+    previous y_k and writes every v_k; prox (the scan in projection mode, all
+    blocks) reads v_k and a_k and writes the new y_k.
+
+    BCD and FISTA add one update-kind launch per checked iteration that reads
+    w and all duals and writes the primal ("eval")."""
     if algo == "bcd":
-        return {"prox": 12, "update": 4 * ndim + 4}
-    return {"prox": 12 * ndim, "update": 4 + 12 * ndim}
+        return {"prox": 12, "update": 4 * ndim + 4, "eval": 4 * ndim + 8, "check_extra": 0}
+    if algo == "fista":
+        return {"prox": 12 * ndim, "update": 4 + 12 * ndim, "eval": 4 * ndim + 8, "check_extra": 0}
+    return {"prox": 12 * ndim, "update": 4 + 12 * ndim, "eval": None, "check_extra": 4}
 
 
 def peaks():
@@ -146,7 +154,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-ALGOS = {"aar": 0, "ap": 1, "bcd": 2}
+ALGOS = {"aar": 0, "ap": 1, "bcd": 2, "fista": 3}
 
 
 def cpu_leg(name, w, a, budget_s=12.0, algo="aar"):
@@ -564,17 +572,19 @@ def run_ours(args):
     # roofline of the dominant kernel (largest device-time share)
     kinds = ["prox", "update", "check", "other"]
     bpv = kernel_bytes_per_vertex(ndim, args.algo)
+    evals = args.steps if bpv["eval"] is not None else 0       # one checked iteration per step
+    kind_bytes = [bpv["prox"] * klaunch[0] * n,
+                  (bpv["update"] * (klaunch[1] - evals) + (bpv["eval"] or 0) * evals
+                   + bpv["check_extra"] * args.steps) * n]
     dom = max(range(2), key=lambda k: kms[k])
     dom_name = kinds[dom]
     launches = int(klaunch[dom])
-    alg_bytes = bpv[dom_name] * n
-    if dom_name == "update":
-        alg_bytes += 4 * n * args.steps / max(launches, 1)      # one checked iteration per step
+    alg_bytes = kind_bytes[dom] / max(launches, 1)
     avg_s = kms[dom] / 1e3 / max(launches, 1)
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_kind = peaks()
     traffic = kernel_traffic(dom_name, args.workload if args.algo == "aar" else f"{args.workload}:{args.algo}")
-    moved = (bpv["prox"] * klaunch[0] + bpv["update"] * klaunch[1] + 4 * args.steps) * n
+    moved = kind_bytes[0] + kind_bytes[1]
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
@@ -639,7 +649,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="volume256")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--algo", choices=sorted(ALGOS), default="aar",
-                    help="iteration of the volume256/seg1024 workloads: AAR (Eq. 3), AP (Sec. 4.2), BCD (Sec. 4.1)")
+                    help="iteration of the volume256/seg1024 workloads: AAR (Eq. 3), AP (Sec. 4.2), BCD or FISTA (Sec. 4.1)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -62,13 +62,18 @@ typedef enum {
 
 enum { TVCUT_I32 = 0, TVCUT_F32 = 1, TVCUT_F64 = 2 };    /* element types */
 enum { TVCUT_HOST = 0, TVCUT_DEVICE = 1 };                /* pointer space */
-enum { TVCUT_AAR = 0, TVCUT_AP = 1, TVCUT_BCD = 2 };      /* algorithms    */
+enum { TVCUT_AAR = 0, TVCUT_AP = 1, TVCUT_BCD = 2, TVCUT_FISTA = 3 };  /* algorithms */
 
 typedef struct {
     int algo;            /* TVCUT_AAR (Eq. 3, default), TVCUT_AP (Sec. 4.2) or
                             TVCUT_BCD (Sec. 4.1, cyclic projections: blocks in
                             turn, y_k <- Pi_{K_k}(w - sum_{j != k} y_j); state y,
-                            cold start 0) */
+                            cold start 0) or TVCUT_FISTA (Sec. 4.1, accelerated
+                            projected gradient on the smooth dual
+                            1/2 ||sum_k y_k - w||^2 with step 1/r:
+                            y <- Pi_K(Pi_L(u)), u = y + ((t_{k-1} - 1)/t_k)(y - y_prev);
+                            state y, cold start 0; one extra ndim*n buffer).
+                            BCD and FISTA need mapping -1, 0, 5 or 6. */
     int iterate_dtype;   /* TVCUT_F32 (default) or TVCUT_F64: precision of the
                             state and of the chain prox; gaps and energies are
                             always accumulated in FP64 (and int64 for exact
@@ -179,8 +184,10 @@ tvcut_status tvcut_cut(tvcut_t h, uint8_t* labels, int space, tvcut_stats* out);
 tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int space);
 
 /* Copy the product-space state (ndim*n values of the iterate type: z for AAR,
- * lambda for AP, the block duals y for BCD) out of / into the handle: checkpoint, resume, and the warm
- * start of Sec. 4.4 (reuse the state of a similar, earlier problem). */
+ * lambda for AP, the block duals y for BCD and FISTA) out of / into the
+ * handle: checkpoint, resume, and the warm start of Sec. 4.4 (reuse the state
+ * of a similar, earlier problem).  Setting a FISTA state restarts its
+ * momentum (previous iterate = the state, t = 1). */
 tvcut_status tvcut_get_state(tvcut_t h, void* s, int space);
 tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
 
@@ -189,8 +196,8 @@ tvcut_status tvcut_set_state(tvcut_t h, const void* s, int space);
  * values of the iterate type in grid layout.  These are the y_i that Sec. 4.4
  * reuses to warm-start a similar problem: tvcut_set_state(h2, y) starts h2
  * from them.  (Reusing the state itself also carries its divergent part,
- * which grows with the iteration count, Sec. 4.3.)  For TVCUT_BCD the state
- * is already y and this copies it.  Errors: STATE, CUDA. */
+ * which grows with the iteration count, Sec. 4.3.)  For TVCUT_BCD and
+ * TVCUT_FISTA the state is already y and this copies it.  Errors: STATE, CUDA. */
 tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space);
 
 /* Warm start from a predicted primal xhat (n FP32 values): every block gets

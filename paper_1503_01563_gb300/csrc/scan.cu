@@ -498,7 +498,74 @@ cudaError_t launch_bcd_prepare(const UpdateArgs<T>& A, int skip, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// FISTA on the smooth dual (Sec. 4.1): g(y) = 1/2 ||sum_k y_k - w||^2 has the
+// same gradient sum_j u_j - w in every block and Lipschitz constant r, so the
+// gradient step from the extrapolated point u is Pi_L(u).  Per vertex, for all
+// blocks: u_k = y_k + beta (y_k - p_k), v_k = u_k + (w - sum_j u_j) / r.  The
+// scan then writes Pi_{K_k}(v_k) over p (the buffers swap roles afterwards).
+template <typename T, int R_>
+__global__ void __launch_bounds__(kUpdThreads) fista_prepare_kernel(FistaArgs<T> A)
+{
+    __shared__ T sy[kTile][kTile + 1];
+    __shared__ T sp[kTile][kTile + 1];
+    const int64_t R = A.rows, W = A.cols;
+    const int64_t tiles_c = (W + kTile - 1) / kTile;
+    const int64_t r0 = (blockIdx.x / tiles_c) * kTile;
+    const int64_t c0 = (blockIdx.x % tiles_c) * kTile;
+    constexpr int last = R_ - 1;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+#pragma unroll
+    for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+        const int64_t c = c0 + cc, r = r0 + tx;
+        if (c < W && r < R) {
+            sy[cc][tx] = A.y[last][c * R + r];
+            sp[cc][tx] = A.p[last][c * R + r];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTile; rr += kUpdThreads / kTile) {
+        const int64_t r = r0 + rr, c = c0 + tx;
+        if (r >= R || c >= W) continue;
+        const int64_t g = r * W + c;
+        T u[R_];
+        T usum = T(0);
+#pragma unroll
+        for (int k = 0; k < R_; ++k) {
+            const T yv = (k == last) ? sy[tx][rr] : A.y[k][g];
+            const T pv = (k == last) ? sp[tx][rr] : A.p[k][g];
+            u[k] = yv + A.beta * (yv - pv);
+            usum += u[k];
+        }
+        const T corr = (A.w[g] - usum) / T(R_);
+#pragma unroll
+        for (int k = 0; k < R_; ++k) {
+            const T vv = u[k] + corr;
+            if (k == last) sy[tx][rr] = vv;
+            else A.v[k][g] = vv;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+        const int64_t c = c0 + cc, r = r0 + tx;
+        if (c < W && r < R) A.v[last][c * R + r] = sy[cc][tx];
+    }
+}
+
+template <typename T>
+cudaError_t launch_fista_prepare(const FistaArgs<T>& A, cudaStream_t s)
+{
+    const int64_t tiles = ((A.rows + kTile - 1) / kTile) * ((A.cols + kTile - 1) / kTile);
+    if (tiles == 0) return cudaSuccess;
+    if (A.r == 3) fista_prepare_kernel<T, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A);
+    else if (A.r == 2) fista_prepare_kernel<T, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 #define TVCUT_SCAN_INST(T)                                                                  \
+    template cudaError_t launch_fista_prepare<T>(const FistaArgs<T>&, cudaStream_t);        \
     template cudaError_t launch_bcd_prepare<T>(const UpdateArgs<T>&, int, cudaStream_t);    \
     template cudaError_t launch_scan<T>(ScanArgs<T>, cudaStream_t);                         \
     template cudaError_t launch_update<T>(int, const UpdateArgs<T>&, cudaStream_t);         \

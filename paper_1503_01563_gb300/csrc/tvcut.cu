@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "tvcut_internal.cuh"
@@ -34,6 +35,9 @@ struct tvcut_ctx {
     int64_t a_len[3] = {0, 0, 0};
     void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
     void* xk = nullptr;            // ndim * n: per-block prox outputs of the scan schedule
+    void* yprev = nullptr;         // FISTA: ndim * n, the previous iterate (swaps with state)
+    double fista_tprev = 1.0;      // FISTA momentum sequence: t_{k-1} and t_k of the next step
+    double fista_t = 1.0;
     bool tlast = true;             // scan schedule: block ndim-1 (state, weights) stored transposed
     uint8_t* labels = nullptr;     // n
     CheckPartial* partials = nullptr;
@@ -109,6 +113,7 @@ extern "C" void tvcut_destroy(tvcut_t h)
     for (int k = 0; k < 3; ++k) cudaFree(h->a[k]);
     cudaFree(h->scratch);
     cudaFree(h->xk);
+    cudaFree(h->yprev);
     cudaFree(h->labels);
     cudaFree(h->partials);
     cudaFree(h->level_partials);
@@ -121,8 +126,14 @@ extern "C" void tvcut_destroy(tvcut_t h)
 
 static bool valid_params(const tvcut_params* p, std::string& why)
 {
-    if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP && p->algo != TVCUT_BCD) { why = "params.algo must be TVCUT_AAR, TVCUT_AP or TVCUT_BCD"; return false; }
-    if (p->algo == TVCUT_BCD && p->mapping >= 1 && p->mapping <= 4) { why = "TVCUT_BCD runs on the scan schedule (mapping -1, 0, 5 or 6)"; return false; }
+    if (p->algo != TVCUT_AAR && p->algo != TVCUT_AP && p->algo != TVCUT_BCD && p->algo != TVCUT_FISTA) {
+        why = "params.algo must be TVCUT_AAR, TVCUT_AP, TVCUT_BCD or TVCUT_FISTA";
+        return false;
+    }
+    if ((p->algo == TVCUT_BCD || p->algo == TVCUT_FISTA) && p->mapping >= 1 && p->mapping <= 4) {
+        why = "TVCUT_BCD and TVCUT_FISTA run on the scan schedule (mapping -1, 0, 5 or 6)";
+        return false;
+    }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
     if (p->mapping < -1 || p->mapping > 6) { why = "params.mapping must be -1 (auto) or 0..6"; return false; }
@@ -172,6 +183,7 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
     if (e == cudaSuccess) e = cudaMalloc(&h->xk, es * (size_t)(ndim * n));
+    if (e == cudaSuccess && prm.algo == TVCUT_FISTA) e = cudaMalloc(&h->yprev, es * (size_t)(ndim * n));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->labels, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(CheckPartial) * kCheckBlocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->level_partials, sizeof(LevelPartial) * kCheckBlocks);
@@ -295,6 +307,16 @@ static tvcut_status ingest(tvcut_t h, const void* src, int dtype, int space, int
     return TVCUT_OK;
 }
 
+// FISTA: start the momentum afresh from the current state (previous iterate =
+// current, t = 1), as at a cold start; a no-op for the other methods.
+static cudaError_t restart_momentum(tvcut_t h)
+{
+    h->fista_tprev = h->fista_t = 1.0;
+    if (h->p.algo != TVCUT_FISTA) return cudaSuccess;
+    return cudaMemcpyAsync(h->yprev, h->state, (size_t)h->esize * (size_t)(h->ndim * h->n),
+                           cudaMemcpyDeviceToDevice, h->stream);
+}
+
 template <typename T>
 static tvcut_status cold_start(tvcut_t h)
 {
@@ -307,6 +329,7 @@ static tvcut_status cold_start(tvcut_t h)
     } else {
         CK(h, cudaMemsetAsync(h->state, 0, (size_t)h->esize * (size_t)(h->ndim * h->n), h->stream), "cold start");
     }
+    CK(h, restart_momentum(h), "cold start");
     h->iters = 0;
     h->x_valid = h->labels_valid = false;
     return TVCUT_OK;
@@ -390,21 +413,75 @@ static cudaError_t run_bcd(tvcut_t h, int check)
     return cudaSuccess;
 }
 
+// x = w - sum_k y_k of a state that holds the block duals (BCD, FISTA).
+template <typename T>
+static cudaError_t primal_of_duals(tvcut_t h)
+{
+    UpdateArgs<T> U;
+    memset(&U, 0, sizeof(U));
+    U.rows = rows_of(h);
+    U.cols = cols_of(h);
+    U.r = h->ndim;
+    for (int k = 0; k < h->ndim; ++k) U.s[k] = S_of<T>(h, k);
+    U.w = (const T*)h->w;
+    U.xout = X_of<T>(h);
+    return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
+}
+
+// One FISTA step on the smooth dual (Sec. 4.1): v = Pi_L(y + beta (y - y_prev))
+// for all blocks, then y_prev <- Pi_K(v) by the scan (all blocks in one
+// launch, projection mode), then the two buffers swap so that the state holds
+// the new iterate.  beta = (t_{k-1} - 1) / t_k with t_0 = t_1 = 1.
+template <typename T>
+static cudaError_t run_fista(tvcut_t h, int check)
+{
+    const int r = h->ndim;
+    FistaArgs<T> F;
+    memset(&F, 0, sizeof(F));
+    F.rows = rows_of(h);
+    F.cols = cols_of(h);
+    F.r = r;
+    F.beta = (T)((h->fista_tprev - 1.0) / h->fista_t);
+    for (int k = 0; k < r; ++k) {
+        F.y[k] = S_of<T>(h, k);
+        F.p[k] = (const T*)h->yprev + (int64_t)k * h->n;
+        F.v[k] = XK_of<T>(h, k);
+    }
+    F.w = (const T*)h->w;
+    cudaError_t e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_fista_prepare<T>(F, h->stream); });
+    if (e != cudaSuccess) return e;
+    ScanArgs<T> S;
+    memset(&S, 0, sizeof(S));
+    S.naxes = r;
+    S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
+    S.shadow = 1;
+    for (int k = 0; k < r; ++k) {
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        S.ax[k].nchains = g.nchains;
+        S.ax[k].inner = g.inner;
+        S.ax[k].m = g.m;
+        S.ax[k].transposed = k == r - 1 ? 1 : 0;
+        S.ax[k].v = XK_of<T>(h, k);
+        S.ax[k].a = (const T*)h->a[k];
+        S.ax[k].x = (T*)h->yprev + (int64_t)k * h->n;
+    }
+    e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
+    if (e != cudaSuccess) return e;
+    std::swap(h->state, h->yprev);
+    h->fista_tprev = h->fista_t;
+    h->fista_t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * h->fista_t * h->fista_t));
+    return check ? primal_of_duals<T>(h) : cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t run_iteration(tvcut_t h, int mode, int check)
 {
+    if (h->p.algo == TVCUT_FISTA) {
+        if (mode == UPD_EVAL) return primal_of_duals<T>(h);
+        return run_fista<T>(h, check);
+    }
     if (h->p.algo == TVCUT_BCD) {
-        if (mode == UPD_EVAL) {           // primal of the current duals
-            UpdateArgs<T> U;
-            memset(&U, 0, sizeof(U));
-            U.rows = rows_of(h);
-            U.cols = cols_of(h);
-            U.r = h->ndim;
-            for (int k = 0; k < h->ndim; ++k) U.s[k] = S_of<T>(h, k);
-            U.w = (const T*)h->w;
-            U.xout = X_of<T>(h);
-            return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
-        }
+        if (mode == UPD_EVAL) return primal_of_duals<T>(h);     // primal of the current duals
         return run_bcd<T>(h, check);
     }
     if (!h->tlast) {
@@ -747,7 +824,8 @@ extern "C" tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space)
     if (!y) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: NULL output");
     if (space != TVCUT_HOST && space != TVCUT_DEVICE) return fail(h, TVCUT_ERR_INVALID, "tvcut_get_dual: bad space");
     if (!inputs_ready(h)) return fail(h, TVCUT_ERR_STATE, "tvcut_get_dual: unary and all edge weights must be set first");
-    if (h->p.algo == TVCUT_BCD) return DISPATCH(h, get_state_impl, h, y, space);   // the BCD state is y itself
+    if (h->p.algo == TVCUT_BCD || h->p.algo == TVCUT_FISTA)
+        return DISPATCH(h, get_state_impl, h, y, space);     // the BCD and FISTA states are y itself
     return DISPATCH(h, get_dual_impl, h, y, space);
 }
 
@@ -759,6 +837,7 @@ static tvcut_status set_state_impl(tvcut_t h, const void* s, int space)
        "tvcut_set_state");
     if (h->tlast)
         CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_set_state");
+    CK(h, restart_momentum(h), "tvcut_set_state");
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_set_state");
     h->x_valid = h->labels_valid = false;
     return TVCUT_OK;
@@ -786,6 +865,7 @@ static tvcut_status warmstart_impl(tvcut_t h, const float* xhat, float tau, int 
        "tvcut_warmstart_primal");
     if (h->tlast)
         CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_warmstart_primal");
+    CK(h, restart_momentum(h), "tvcut_warmstart_primal");
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_warmstart_primal");
     h->x_valid = h->labels_valid = false;
     h->iters = 0;

@@ -175,6 +175,21 @@ cudaError_t launch_transpose(const T* in, T* out, int64_t rows, int64_t cols, cu
 template <typename T>
 cudaError_t launch_bcd_prepare(const UpdateArgs<T>& args, int skip, cudaStream_t s);
 
+// FISTA step inputs (scan-schedule layout: the last block transposed).
+template <typename T>
+struct FistaArgs {
+    int64_t rows;
+    int64_t cols;
+    int r;
+    T beta;                // extrapolation weight (t_{k-1} - 1) / t_k
+    const T* y[3];         // current iterate y_k
+    const T* p[3];         // previous iterate y_{k-1}
+    T* v[3];               // out: Pi_L(y + beta (y - p)), the point the scan projects
+    const T* w;
+};
+template <typename T>
+cudaError_t launch_fista_prepare(const FistaArgs<T>& args, cudaStream_t s);
+
 ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
 
 }  // namespace tvcut

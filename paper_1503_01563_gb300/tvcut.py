@@ -21,7 +21,7 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_TIMEOUT = -1, -2, -3, -4, -5
 I32, F32, F64 = 0, 1, 2
 HOST, DEVICE = 0, 1
-AAR, AP, BCD = 0, 1, 2
+AAR, AP, BCD, FISTA = 0, 1, 2, 3
 
 EXPORTED = [
     "tvcut_default_params", "tvcut_create", "tvcut_destroy", "tvcut_last_error",
