@@ -56,22 +56,29 @@ __device__ CheckPartial block_reduce(CheckPartial p)
 
 // One pass over the grid: labels at the plain threshold, the FP64 sums of the
 // check (discrete lower bound, y^T x, f(x), max |x|) and the energies of the
-// level sets [x > levels[j]] (Sec. 2.1: every level set of a solution of the
-// relaxation solves (D)); level 0 is the plain threshold.  Each warp walks
-// whole rows of the last axis, so a vertex's neighbours along every axis are
-// at fixed offsets (+1, +W, +H*W) and the row's coordinates come from one
-// division per row.  A vertex's level labels form a bit mask; an edge adds
-// its weight to the levels whose bit differs at its two ends.  Integer
-// problems accumulate level energies in exact int64, others in FP64.
+// level sets [x > levels[q]] (Sec. 2.1: every level set of a solution of the
+// relaxation solves (D)) for an ascending ladder that contains the plain
+// threshold.  The level index q(v) = #{levels below v} gives a value's labels
+// at every level at once ([v > level_j] = [j < q(v)]), so an edge's ends
+// differ exactly on the levels in [min q, max q) and a vertex is labelled 1 on
+// the levels below its q.  Both are intervals, kept as per-thread difference
+// arrays: entry 0, the common case, lives in a register, and the other
+// entries are touched only by values inside the ladder's range.  Each warp
+// walks whole rows of the last axis, so a vertex's neighbours along every
+// axis are at fixed offsets (+1 from the next lane, +W, +H*W).  Integer
+// problems accumulate level energies in exact int64, others in FP64; every
+// sum has a fixed order.
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
 {
     using Acc = typename std::conditional<EXACT, long long, double>::type;
     CheckPartial acc{0, 0, 0, 0, 0, 0, 0, 0};
-    Acc el[kMaxLevels];
-    int n1l[kMaxLevels];
-#pragma unroll
-    for (int j = 0; j < kMaxLevels; ++j) { el[j] = 0; n1l[j] = 0; }
+    Acc dE[kMaxLevels + 1];
+    int dN[kMaxLevels + 1];
+    for (int q = 0; q <= kMaxLevels; ++q) { dE[q] = 0; dN[q] = 0; }
+    Acc e0 = 0;
+    long long n0 = 0;
+    T xabs = T(0);
     const int L = A.nlevels;
     const int nd = A.ndim;
     const int64_t W = A.dims[nd - 1];
@@ -82,71 +89,94 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * kCheckThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kCheckThreads) >> 5;
-    auto mask_of = [&](T xv) {
-        unsigned mk = 0;
+    auto level_of = [&](T v) {
+        int q = 0;
 #pragma unroll
-        for (int j = 0; j < kMaxLevels; ++j)
-            if (j < L && xv > A.levels[j]) mk |= 1u << j;
-        return mk;
+        for (int j = 0; j < kMaxLevels; ++j) q += (j < L && v > A.levels[j]) ? 1 : 0;
+        return q;
     };
-    auto add_edge = [&](double xd, T x2, unsigned mk, bool l, double ae) {
-        acc.tv += ae * fabs(xd - (double)x2);
-        if (l != (x2 > thr)) {
-            acc.energy += ae;
-            acc.energy_i += llrint(ae);
+    auto to_acc = [](T v) -> Acc {
+        if constexpr (!EXACT) return (Acc)v;
+        else if constexpr (sizeof(T) == 4) return (Acc)__float2int_rn((float)v);   // |v| <= 2^24
+        else return (Acc)llrint((double)v);
+    };
+    auto add_edge = [&](double xd, T x2, int q1, int q2, T ae) {
+        acc.tv += (double)ae * fabs(xd - (double)x2);
+        const int lo = min(q1, q2), hi = max(q1, q2);
+        if (lo != hi) {
+            const Acc av = to_acc(ae);
+            if (lo == 0) e0 += av;
+            else dE[lo] += av;
+            if (hi < L) dE[hi] -= av;
         }
-        const unsigned diff = mk ^ mask_of(x2);
-        const Acc av = EXACT ? (Acc)llrint(ae) : (Acc)ae;
-#pragma unroll
-        for (int j = 0; j < kMaxLevels; ++j)
-            if ((diff >> j) & 1u) el[j] += av;
     };
     for (int64_t r = warp; r < R; r += nwarps) {
         const int64_t h = r % Hm;                 // coordinate along axis nd-2
         const int64_t d = r / Hm;                 // coordinate along axis 0 (3D)
-        for (int64_t c = lane; c < W; c += 32) {
+        for (int64_t cb = 0; cb < W; cb += 32) {  // uniform in the warp (shuffles)
+            const int64_t c = cb + lane;
+            const bool in = c < W;
             const int64_t g = r * W + c;
-            const T xg = A.x[g];
-            const bool l = xg > thr;
-            A.labels[g] = (uint8_t)l;
-            const double wg = (double)A.w[g];
+            const T xg = in ? A.x[g] : T(0);
+            const int qg = level_of(xg);
+            T xr = __shfl_down_sync(0xffffffffu, xg, 1);
+            int qr = __shfl_down_sync(0xffffffffu, qg, 1);
+            if (!in) continue;
+            if (lane == 31 && c + 1 < W) {
+                xr = A.x[g + 1];
+                qr = level_of(xr);
+            }
+            A.labels[g] = (uint8_t)(xg > thr);
+            const T wt = A.w[g];
+            const double wg = (double)wt;
             const double xd = (double)xg;
             acc.lb -= fmax(xd, 0.0);
             acc.ytx += (wg - xd) * xd;
-            acc.xabs = fmax(acc.xabs, fabs(xd));
-            if (l) {
-                acc.energy -= wg;
-                acc.energy_i -= llrint(wg);
-                acc.n1 += 1;
+            xabs = fmax(xabs, fabs(xg));
+            if (qg > 0) {
+                const Acc wv = to_acc(wt);
+                e0 -= wv;
+                n0 += 1;
+                if (qg < L) {
+                    dE[qg] += wv;
+                    dN[qg] -= 1;
+                }
             }
-            const unsigned mk = mask_of(xg);
-            const Acc wv = EXACT ? (Acc)llrint(wg) : (Acc)wg;
-#pragma unroll
-            for (int j = 0; j < kMaxLevels; ++j)
-                if ((mk >> j) & 1u) { el[j] -= wv; n1l[j] += 1; }
             // last axis: edge (c, c+1) of row r
             if (c + 1 < W) {
                 const int64_t ai = A.last_transposed ? c * R + r : r * (W - 1) + c;
-                add_edge(xd, A.x[g + 1], mk, l, (double)A.a[nd - 1][ai]);
+                add_edge(xd, xr, qg, qr, A.a[nd - 1][ai]);
             }
             // axis nd-2: edge (h, h+1); compact index ((d*(Hm-1) + h) * W + c)
-            if (h + 1 < Hm) add_edge(xd, A.x[g + W], mk, l, (double)A.a[nd - 2][(d * (Hm - 1) + h) * W + c]);
+            if (h + 1 < Hm) {
+                const T x2 = A.x[g + W];
+                add_edge(xd, x2, qg, level_of(x2), A.a[nd - 2][(d * (Hm - 1) + h) * W + c]);
+            }
             // axis 0 of a 3D grid: edge (d, d+1); compact index = g
-            if (nd == 3 && d + 1 < D0) add_edge(xd, A.x[g + Hm * W], mk, l, (double)A.a[0][g]);
+            if (nd == 3 && d + 1 < D0) {
+                const T x2 = A.x[g + Hm * W];
+                add_edge(xd, x2, qg, level_of(x2), A.a[0][g]);
+            }
         }
     }
+    acc.xabs = (double)xabs;
     CheckPartial rsum = block_reduce<kCheckThreads>(acc);
     if (threadIdx.x == 0) A.partials[blockIdx.x] = rsum;
-    // level partials, one level at a time in a fixed order
+    // level partials: prefix sums of the difference arrays, one level at a
+    // time, each summed over the block in a fixed order
     __shared__ double se[kCheckThreads / 32];
     __shared__ long long sei[kCheckThreads / 32];
     __shared__ long long sn[kCheckThreads / 32];
     const int wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < kMaxLevels; ++j) {
-        if (j >= L) break;
-        Acc a = el[j];
-        long long c = n1l[j];
+    Acc run = e0;
+    long long rn = n0;
+    for (int q = 0; q < L; ++q) {
+        if (q > 0) {
+            run += dE[q];
+            rn += dN[q];
+        }
+        Acc a = run;
+        long long c = rn;
         for (int dd = 16; dd > 0; dd >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, dd);
             c += __shfl_down_sync(0xffffffffu, c, dd);
@@ -167,9 +197,9 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
                 tc += sn[w];
             }
             if (EXACT) ta = (double)tb;
-            A.level_partials[blockIdx.x].energy[j] = ta;
-            A.level_partials[blockIdx.x].energy_i[j] = tb;
-            A.level_partials[blockIdx.x].n1[j] = tc;
+            A.level_partials[blockIdx.x].energy[q] = ta;
+            A.level_partials[blockIdx.x].energy_i[q] = tb;
+            A.level_partials[blockIdx.x].n1[q] = tc;
         }
     }
 }

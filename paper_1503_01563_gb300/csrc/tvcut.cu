@@ -540,23 +540,29 @@ static tvcut_status run_check(tvcut_t h)
     C.threshold = (T)h->p.threshold;
     C.last_transposed = h->tlast ? 1 : 0;
     C.partials = h->partials;
-    // level-set ladder: threshold, then threshold +- S 10^-j, j = 2, 3, ...
+    // level-set ladder: threshold, then threshold +- S 10^-j, j = 2, 3, ...;
+    // the kernel takes it in ascending order of the iterate-type values
     double lv[kMaxLevels];
     int L = 0;
+    lv[L++] = h->p.threshold;
     if (h->p.level_sets > 0 && h->wmax > 0.0) {
-        lv[L++] = h->p.threshold;
         for (int j = 0; j < h->p.level_sets; ++j) {
             const double d = h->wmax * pow(10.0, -(double)(j + 2));
             lv[L++] = h->p.threshold + d;
             lv[L++] = h->p.threshold - d;
         }
     }
+    int order[kMaxLevels], pos[kMaxLevels];
+    for (int j = 0; j < L; ++j) order[j] = j;
+    for (int i = 1; i < L; ++i)                          // stable insertion sort
+        for (int j = i; j > 0 && (T)lv[order[j - 1]] > (T)lv[order[j]]; --j) std::swap(order[j - 1], order[j]);
+    for (int q = 0; q < L; ++q) pos[order[q]] = q;
     C.nlevels = L;
-    for (int j = 0; j < L; ++j) C.levels[j] = (T)lv[j];
+    for (int q = 0; q < L; ++q) C.levels[q] = (T)lv[order[q]];
     C.level_partials = h->level_partials;
     bool exact_data = h->int_w;
     for (int k = 0; k < h->ndim; ++k) exact_data = exact_data && h->int_a[k];
-    CK(h, traced(h, TVCUT_K_CHECK, L > 0 ? 3 : 2, [&] { return launch_check<T>(C, exact_data, h->dstatus, h->stream); }),
+    CK(h, traced(h, TVCUT_K_CHECK, 3, [&] { return launch_check<T>(C, exact_data, h->dstatus, h->stream); }),
        "check");
     CK(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream), "check");
     CK(h, cudaStreamSynchronize(h->stream), "check");
@@ -567,25 +573,22 @@ static tvcut_status run_check(tvcut_t h)
     bool exact = h->int_w;
     for (int k = 0; k < h->ndim; ++k) exact = exact && h->int_a[k];
     st.iters = h->iters;
-    st.energy = s.energy;
-    st.energy_i64 = s.energy_i;
-    st.n_label1 = s.n1;
-    st.threshold = h->p.threshold;
-    // keep the lowest-energy level set (ties: the plain threshold)
-    int best = 0;
+    // keep the lowest-energy level set; ties go to the earlier ladder entry
+    // (the plain threshold first)
     const LevelPartial& lp = h->hstatus->levels;
+    int best = 0;
     for (int j = 1; j < L; ++j) {
-        const bool lower = exact ? lp.energy_i[j] < lp.energy_i[best] : lp.energy[j] < lp.energy[best];
+        const int qj = pos[j], qb = pos[best];
+        const bool lower = exact ? lp.energy_i[qj] < lp.energy_i[qb] : lp.energy[qj] < lp.energy[qb];
         if (lower) best = j;
     }
-    if (best > 0) {
-        st.energy = lp.energy[best];
-        st.energy_i64 = lp.energy_i[best];
-        st.n_label1 = lp.n1[best];
-        st.threshold = lv[best];
+    st.energy = lp.energy[pos[best]];
+    st.energy_i64 = lp.energy_i[pos[best]];
+    st.n_label1 = lp.n1[pos[best]];
+    st.threshold = lv[best];
+    if (best > 0)
         CK(h, traced(h, TVCUT_K_CHECK, 1, [&] { return launch_labels<T>(X_of<T>(h), (T)lv[best], h->labels, h->n, h->stream); }),
            "check");
-    }
     st.energy_exact = exact ? 1 : 0;
     st.discrete_lb = s.lb;
     st.tv_value = s.tv;

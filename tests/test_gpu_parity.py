@@ -151,6 +151,31 @@ def test_check_statistics(tv, orc):
         assert st.n_label1 == int(lab.sum())
 
 
+@pytest.mark.parametrize("dims", [(31, 29), (9, 10, 11), (1, 40), (33, 1)])
+@pytest.mark.parametrize("level_sets", [0, 8])
+def test_check_statistics_f32(tv, orc, dims, level_sets):
+    """FP32 iterates: the check's sums are FP64 over the FP32 primal, so they
+    agree with the oracle's sums over the same primal to FP64 rounding; the
+    energies on integer data exactly."""
+    w, a = inputs.uniform_grid(dims, 15)
+    s = tv.Solver(dims, dtype=tv.F32, check_every=1, level_sets=level_sets)
+    s.set_problem(w, a)
+    for k in (1, 6, 25):
+        _, st = s.iterate(k)
+        lab, _ = s.cut()
+        x = s.primal()
+        assert np.array_equal(lab, (x > st.threshold).astype(np.uint8))
+        assert st.energy_i64 == orc.energy(w, a, lab)
+        assert st.n_label1 == int(lab.sum())
+        y = w - x
+        assert abs(st.discrete_lb - np.minimum(y - w, 0).sum()) < 1e-9 * max(1, abs(st.discrete_lb))
+        f = orc.tv_value(a, x)
+        assert abs(st.tv_value - f) < 1e-9 * max(1, f)
+        assert abs(st.tv_gap - (f - (y * x).sum())) < 1e-9 * max(1, f)
+        assert st.x_absmax == np.abs(x).max()
+    s.close()
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_exact_cut_64(tv, orc, seed):
     """64x64, w in [-50, 50], a in [1, 20]: the FP64 GPU cut energy equals the
