@@ -73,7 +73,7 @@ typedef struct {
                             1/2 ||sum_k y_k - w||^2 with step 1/r:
                             y <- Pi_K(Pi_L(u)), u = y + ((t_{k-1} - 1)/t_k)(y - y_prev);
                             state y, cold start 0; one extra ndim*n buffer).
-                            BCD and FISTA need mapping -1, 0, 5 or 6. */
+                            BCD and FISTA need mapping -1, 0 or 5..9. */
     int iterate_dtype;   /* TVCUT_F32 (default) or TVCUT_F64: precision of the
                             state and of the chain prox; gaps and energies are
                             always accumulated in FP64 (and int64 for exact
@@ -88,8 +88,9 @@ typedef struct {
                             update launch; the scan gives each chain a thread,
                             or, when there are too few chains to fill the GPU,
                             a warp (speculative pieces, see csrc/scan.cu);
-                            5, 6: that schedule with thread-per-chain or
-                            warp-per-chain scans forced; 1, 2, 3: one fused
+                            5: that schedule with thread-per-chain scans
+                            forced; 6, 7, 8, 9: with 32, 16, 8 or 4 lanes per
+                            chain (speculative pieces) forced; 1, 2, 3: one fused
                             sweep per block (prox and update in the same pass)
                             on shared-memory tiles of 8, 16, 32 chains; 4: the
                             fused sweeps with one thread per chain reading

@@ -153,10 +153,12 @@ __device__ __forceinline__ int lane_scan(LaneState<T>& st, int m, int stop, cons
     }
 }
 
-constexpr int kWarpChains = 8;      // chains (warps) per CTA of the warp scan
 
-template <typename T, bool SHADOW>
-__global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, int nc)
+// G lanes share a chain (G = 4 .. 32, a warp holds 32/G chains); a CTA holds
+// nc chains, nc * G threads.  With few chains G = 32 spreads each chain over a
+// whole warp; with many, a smaller G does less speculative work per chain.
+template <typename T, bool SHADOW, int G>
+__global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
 {
     extern __shared__ __align__(16) unsigned char wsm[];
     int k = 0;
@@ -193,20 +195,22 @@ __global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, 
     scan_cp_wait();
     __syncthreads();
 
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (wid >= nvalid) return;
-    int64_t vb, ab, gst;
-    gbase(c0 + wid, vb, ab, gst);
+    // lanes of chains past the end stay (inactive) for the group shuffles
+    const int ch = threadIdx.x / G, gl = threadIdx.x % G;
+    const int glane0 = (threadIdx.x & 31) & ~(G - 1);     // first warp lane of the group
+    const bool valid = ch < nvalid;
+    int64_t vb = 0, ab = 0, gst = 0;
+    if (valid) gbase(c0 + ch, vb, ab, gst);
     T* gx = X.x + vb;
-    const T* cv = sv + wid * pitch;
-    const T* ca = sa + wid * pitch;
-    uint8_t* cc = code + wid * m;
-    const int lp = (m + 31) / 32;                 // piece length
-    const int npieces = (m + lp - 1) / lp;
-    const int p0 = lane * lp;
+    const T* cv = sv + ch * pitch;
+    const T* ca = sa + ch * pitch;
+    uint8_t* cc = code + ch * m;
+    const int lp = (m + G - 1) / G;               // piece length
+    const int npieces = valid ? (m + lp - 1) / lp : 0;
+    const int p0 = gl * lp;
     const int p1 = min(m, p0 + lp);
-    const bool active = lane < npieces;
-    const bool lastp = lane == npieces - 1;
+    const bool active = gl < npieces;
+    const bool lastp = gl == npieces - 1;
     auto write_seg = [&](int from, int to, T t) {
         for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = SHADOW ? cv[skew32(j)] - t : t;
     };
@@ -234,15 +238,20 @@ __global__ void __launch_bounds__(32 * kWarpChains) wscan_kernel(ScanArgs<T> A, 
         });
     }
     // verified pieces: lane 0, then the piece holding each verified lane's
-    // merge bend (pieces skipped over are rewritten by that continuation)
+    // merge bend (pieces skipped over are rewritten by that continuation);
+    // G steps for every group, so that the whole warp shuffles together
     const int target = (active && !lastp && merge < m - 1) ? merge / lp : npieces;
     unsigned verified = 0;
-    for (int v = 0; v < npieces;) {
-        verified |= 1u << v;
-        v = __shfl_sync(0xffffffffu, target, v);
+    int v = 0;
+#pragma unroll 1
+    for (int it = 0; it < G; ++it) {
+        const bool live = v < npieces;
+        if (live) verified |= 1u << v;
+        const int nv = __shfl_sync(0xffffffffu, target, glane0 + (live ? v : 0));
+        if (live) v = nv;
     }
     // phase 3: verified lanes rewrite their continuation up to the merge bend
-    if (((verified >> lane) & 1u) && active && !lastp) {
+    if (((verified >> gl) & 1u) && active && !lastp) {
         lane_scan<T>(st, m, m, cv, ca, [&](int s0, int e, int, T t) {
             write_seg(s0, e, t);
             return e >= merge;
@@ -254,6 +263,38 @@ template <typename T>
 static size_t wscan_smem(int m, int nc)
 {
     return (size_t)nc * (2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
+}
+
+// Chains per CTA for G lanes per chain: at most 256 threads, whole warps, and
+// shared memory within 100 KB (two CTAs per SM); 0 if a warp's chains do not fit.
+template <typename T>
+static int wscan_chains(int m, int G)
+{
+    const int per_warp = 32 / G;
+    int nc = 256 / G;
+    while (nc > per_warp && wscan_smem<T>(m, nc) > 100 * 1024) nc -= per_warp;
+    return wscan_smem<T>(m, nc) <= 200 * 1024 ? nc : 0;
+}
+
+template <typename T, bool SHADOW>
+static cudaError_t launch_wscan(const ScanArgs<T>& wrp, int G, int nc, int64_t blocks, size_t smem, cudaStream_t s)
+{
+    static bool attr_set[64][4] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int gi = G == 32 ? 0 : G == 16 ? 1 : G == 8 ? 2 : 3;
+    void (*fn)(ScanArgs<T>, int) = G == 32 ? wscan_kernel<T, SHADOW, 32>
+                                   : G == 16 ? wscan_kernel<T, SHADOW, 16>
+                                   : G == 8 ? wscan_kernel<T, SHADOW, 8>
+                                            : wscan_kernel<T, SHADOW, 4>;
+    if (dev < 0 || dev >= 64 || !attr_set[dev][gi]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev][gi] = true;
+    }
+    fn<<<(unsigned)blocks, nc * G, smem, s>>>(wrp, nc);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -272,7 +313,7 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
         const ScanAxis<T>& X = A.ax[k];
         bool warp = X.m >= 64 && total <= 98304 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
         if (A.force == 1) warp = false;
-        if (A.force == 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        if (A.force >= 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
         if (warp) wrp.ax[wrp.naxes++] = X;
         else thr.ax[thr.naxes++] = X;
     }
@@ -292,30 +333,26 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
     if (wrp.naxes) {
         int mmax = 0;
         for (int k = 0; k < wrp.naxes; ++k) mmax = max(mmax, wrp.ax[k].m);
-        int nc = kWarpChains;
-        while (nc > 1 && wscan_smem<T>(mmax, nc) > 100 * 1024) nc /= 2;
+        // automatic: pieces of about 16 elements (measured on 256^3 and 128^3
+        // grids and 1024^2 images: fewer pieces per chain do less speculative
+        // work, shorter ones keep more lanes busy)
+        int G = 32;
+        if (A.force == 0) while (G > 4 && mmax < 16 * G) G >>= 1;
+        else G = A.force == 3 ? 16 : A.force == 4 ? 8 : A.force == 5 ? 4 : 32;
+        int nc = wscan_chains<T>(mmax, G);
+        if (nc == 0) {                             // long chains: whole warps
+            G = 32;
+            nc = wscan_chains<T>(mmax, G);
+        }
         int64_t blocks = 0;
         for (int k = 0; k < wrp.naxes; ++k) {
             wrp.ax[k].block_begin = blocks;
             blocks += (wrp.ax[k].nchains + nc - 1) / nc;
         }
         const size_t smem = wscan_smem<T>(mmax, nc);
-        static bool attr_set[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-            e = cudaFuncSetAttribute(wscan_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(wscan_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) attr_set[dev] = true;
-        }
-        if (blocks > 0) {
-            if (A.shadow) wscan_kernel<T, true><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
-            else wscan_kernel<T, false><<<(unsigned)blocks, 32 * nc, smem, s>>>(wrp, nc);
-            return cudaGetLastError();
-        }
+        if (blocks > 0)
+            return A.shadow ? launch_wscan<T, true>(wrp, G, nc, blocks, smem, s)
+                            : launch_wscan<T, false>(wrp, G, nc, blocks, smem, s);
     }
     return cudaSuccess;
 }

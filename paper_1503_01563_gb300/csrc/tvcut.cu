@@ -131,12 +131,12 @@ static bool valid_params(const tvcut_params* p, std::string& why)
         return false;
     }
     if ((p->algo == TVCUT_BCD || p->algo == TVCUT_FISTA) && p->mapping >= 1 && p->mapping <= 4) {
-        why = "TVCUT_BCD and TVCUT_FISTA run on the scan schedule (mapping -1, 0, 5 or 6)";
+        why = "TVCUT_BCD and TVCUT_FISTA run on the scan schedule (mapping -1, 0 or 5..9)";
         return false;
     }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
-    if (p->mapping < -1 || p->mapping > 6) { why = "params.mapping must be -1 (auto) or 0..6"; return false; }
+    if (p->mapping < -1 || p->mapping > 9) { why = "params.mapping must be -1 (auto) or 0..9"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
@@ -210,6 +210,8 @@ static T* S_of(tvcut_t h, int k) { return (T*)h->state + (int64_t)k * h->n; }
 template <typename T>
 static T* XK_of(tvcut_t h, int k) { return (T*)h->xk + (int64_t)k * h->n; }
 static int64_t cols_of(tvcut_t h) { return h->dims[h->ndim - 1]; }
+// mapping 5: thread per chain; 6, 7, 8, 9: 32, 16, 8, 4 lanes per chain
+static int scan_force(int mapping) { return mapping >= 5 ? mapping - 4 : 0; }
 static int64_t rows_of(tvcut_t h) { return h->n / h->dims[h->ndim - 1]; }
 
 // In-place layout change of an (rows x cols) array through the xk area
@@ -393,7 +395,7 @@ static cudaError_t run_bcd(tvcut_t h, int check)
         ScanArgs<T> S;
         memset(&S, 0, sizeof(S));
         S.naxes = 1;
-        S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
+        S.force = scan_force(h->p.mapping);
         ChainGeom g = chain_geom(h->ndim, h->dims, k);
         S.ax[0].nchains = g.nchains;
         S.ax[0].inner = g.inner;
@@ -453,7 +455,7 @@ static cudaError_t run_fista(tvcut_t h, int check)
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
     S.naxes = r;
-    S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
+    S.force = scan_force(h->p.mapping);
     S.shadow = 1;
     for (int k = 0; k < r; ++k) {
         ChainGeom g = chain_geom(h->ndim, h->dims, k);
@@ -493,7 +495,7 @@ static cudaError_t run_iteration(tvcut_t h, int mode, int check)
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
     S.naxes = r;
-    S.force = h->p.mapping == 5 ? 1 : (h->p.mapping == 6 ? 2 : 0);
+    S.force = scan_force(h->p.mapping);
     for (int k = 0; k < r; ++k) {
         ChainGeom g = chain_geom(h->ndim, h->dims, k);
         S.ax[k].nchains = g.nchains;

@@ -38,7 +38,7 @@ struct ScanAxis {
 template <typename T>
 struct ScanArgs {
     int naxes;
-    int force;             // 0 automatic, 1 thread per chain, 2 warp per chain
+    int force;             // 0 automatic, 1 thread per chain, 2/3/4/5: 32/16/8/4 lanes per chain
     int shadow;            // 1: write v - prox(v) (the projection onto K_k) instead of prox(v)
     ScanAxis<T> ax[3];
 };
