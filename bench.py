@@ -385,8 +385,9 @@ def run_batch(args):
 
 
 def run_warm(args):
-    """Cold-started AAR vs AAR started from the U-Net's predicted block duals,
-    both to the oracle-equal cut, on one GPU."""
+    """Cold-started iteration (AAR by default, --algo) vs the same iteration
+    started from the U-Net's predicted block duals (the AAR/AP state z = y_hat,
+    the BCD/FISTA state y = y_hat), both to the oracle-equal cut, on one GPU."""
     import torch
 
     rank = int(os.environ.get("RANK", "0"))
@@ -405,12 +406,14 @@ def run_warm(args):
     e_star = oracle.maxflow(w, a, 1)[1]
     t_mf = time.perf_counter() - t0
     cores = os.cpu_count() or 1
-    st0 = oracle.cold_state(oracle.AAR, w)
+    algo = ALGOS[args.algo]
+    st0 = oracle.cold_state(algo, w)
     t0 = time.perf_counter()
-    oracle.iterate(oracle.AAR, w, a, st0, 2, nthreads=cores)
+    oracle.iterate(algo, w, a, st0, 2, nthreads=cores)
     t_it = time.perf_counter() - t0
     cpu_base = {"value": 2 * n / t_it / 1e6, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                "sample": f"2 FP64 AAR iterations over the 2048^2 grid ({t_it:.1f} s); max-flow E* {t_mf:.1f} s"}
+                "sample": f"2 FP64 {args.algo.upper()} iterations over the 2048^2 grid ({t_it:.1f} s); "
+                          f"max-flow E* {t_mf:.1f} s"}
     stream = torch.cuda.current_stream()
     # training (untimed): solver-generated targets, GPU forward/backward/Adam
     t0 = time.perf_counter()
@@ -422,7 +425,7 @@ def run_warm(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, Y
-    s = tvcut.Solver(dims, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+    s = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
     s.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
 
     def probe(z0):
@@ -438,7 +441,7 @@ def run_warm(args):
     k_cold = probe(None)
     z0 = learn.predict_state(net, w, a)
     k_warm = probe(z0)
-    timed = tvcut.Solver(dims, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream)
+    timed = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream)
     timed.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
     feats = torch.from_numpy(learn.features(w, a)[0][None]).cuda()
     sc = learn.features(w, a)[1]
@@ -467,7 +470,7 @@ def run_warm(args):
     out = {"metric": "Mvertex-iter/s", "value": n * (k_cold or wl["cap"]) / (cold / 1e3) / 1e6,
            "unit": "Mvertex-iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": cold,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "warm2048", "dims": list(dims), "algo": "AAR", "iterate": "f32",
+           "config": {"workload": "warm2048", "dims": list(dims), "algo": args.algo.upper(), "iterate": "f32",
                       "network": "U-Net 4 levels, 32 channels, BF16 weights/activations, FP32 accumulation",
                       "training": f"{wl['train_n']} solver-generated {wl['train_hw']}^2 problems, "
                                   f"{wl['train_steps']} Adam steps of 16 (data {t_data:.1f} s, training {t_train:.1f} s, "
