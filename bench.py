@@ -222,7 +222,8 @@ def batch_problems(G, seed):
 
 def run_batch(args):
     """512 uneven 2D grids: one batched solve (graph-replayed iterations) vs
-    the same grids solved one after another with one handle each."""
+    the same grids solved one after another with one handle each.  --algo:
+    AAR (default), AP or FISTA (the batched solver has no BCD)."""
     import torch
     import torch.distributed as dist
 
@@ -232,6 +233,9 @@ def run_batch(args):
     if world > 1:
         dist.init_process_group("nccl")
     wl = WORKLOADS["batch512"]
+    if args.algo == "bcd":
+        raise SystemExit("batch512: the batched solver runs AAR, AP or FISTA")
+    algo = ALGOS[args.algo]
     dims, probs = batch_problems(wl["grids"], wl["seed"])
     n_all = int(sum(h * w for h, w in dims))
     if world > 1:                      # grids share nothing: each rank solves its own shard
@@ -254,22 +258,22 @@ def run_batch(args):
         nv, t_it = 0, 0.0
         for g in sample:
             w, a = probs[g]
-            st = oracle.cold_state(oracle.AAR, w)
+            st = oracle.cold_state(algo, w)
             t0 = time.perf_counter()
-            oracle.iterate(oracle.AAR, w, a, st, 5, nthreads=cores)
+            oracle.iterate(algo, w, a, st, 5, nthreads=cores)
             t_it += time.perf_counter() - t0
             nv += 5 * w.size
             if t_it > args.cpu_budget:
                 break
         cpu_base = {"value": nv / t_it / 1e6, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                    "sample": f"5 FP64 AAR iterations on each of up to {len(sample)} of the 512 grids "
+                    "sample": f"5 FP64 {args.algo.upper()} iterations on each of up to {len(sample)} of the 512 grids "
                               f"({t_it:.1f} s); max-flow E* of {len(sample)} sampled grids took {t_mf:.1f} s"}
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1503_01563_gb300 import tvcut
     stream = torch.cuda.current_stream(dev)
     dev_probs = [(torch.from_numpy(w).to(dev), [torch.from_numpy(x).to(dev) for x in a]) for w, a in probs]
-    b = tvcut.Batch(dims, dtype=tvcut.F32, stream=stream.cuda_stream)
+    b = tvcut.Batch(dims, algo=algo, dtype=tvcut.F32, stream=stream.cuda_stream)
     for g, (w, a) in enumerate(dev_probs):
         b.set_problem(g, w, a)
     b.reset()
@@ -320,7 +324,7 @@ def run_batch(args):
     # the same grids solved one by one, one handle each
     singles = []
     for g, (w, a) in enumerate(dev_probs):
-        s = tvcut.Solver(dims[g], dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+        s = tvcut.Solver(dims[g], algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
         s.set_problem(w, a)
         singles.append(s)
     for s in singles[:8]:
@@ -337,7 +341,7 @@ def run_batch(args):
     for s in singles:
         s.close()
     # end to end with host buffers: upload every grid, solve, read every labelling
-    e2e_b = tvcut.Batch(dims, dtype=tvcut.F32, stream=stream.cuda_stream)
+    e2e_b = tvcut.Batch(dims, algo=algo, dtype=tvcut.F32, stream=stream.cuda_stream)
     pinned = [(torch.from_numpy(w).pin_memory(), [torch.from_numpy(x).pin_memory() for x in a]) for w, a in probs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -350,7 +354,7 @@ def run_batch(args):
     e2e_s = time.perf_counter() - t0
     e2e_b.close()
     h2d = int(sum(w.nbytes + sum(x.nbytes for x in a) for w, a in probs))
-    iter_bytes = (24 + 28) * n_total
+    iter_bytes = (24 + 28) * n_total      # scan 24 B + update (FISTA: step) 28 B per vertex
     peak, peak_kind = peaks()
     achieved = iter_bytes * iters / (ms_per_step / 1e3) / 1e9
     if rank == 0:
@@ -358,7 +362,7 @@ def run_batch(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": "batch512", "grids": 512, "vertices": n_all, "algo": "AAR",
+               "config": {"workload": "batch512", "grids": 512, "vertices": n_all, "algo": args.algo.upper(),
                           "parallelism": f"grids sharded over {world} GPU(s), no collective" if world > 1 else "single",
                           "iterate": "f32", "iters_per_step": iters,
                           "step": "cold start + iterations to the oracle-equal cut of the sampled grids + check",
@@ -375,7 +379,7 @@ def run_batch(args):
                "cpu_baseline": cpu_base,
                "e2e": {"value": n_total * iters / e2e_s / 1e6, "unit": "Mvertex-iter/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n_total},
-               "clocks": clk, "gpu_launches": 2 * iters + 3}
+               "clocks": clk, "gpu_launches": (3 * iters + 4) if args.algo == "fista" else (2 * iters + 3)}
         print(json.dumps(out), flush=True)
     b.close()
     if world > 1:

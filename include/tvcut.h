@@ -248,11 +248,15 @@ tvcut_status tvcut_profile_read(tvcut_t h, double* ms, int64_t* launches);
  * vertices; each tvcut_batch_iterate call (its iterations and the closing
  * check) runs as one CUDA graph, captured on first use for that iteration
  * count and replayed afterwards.  Parameters as for tvcut_create (mapping is
- * ignored; tvcut_batch_autotune picks the launch shape). */
+ * ignored; tvcut_batch_autotune picks the launch shape); algo TVCUT_AAR,
+ * TVCUT_AP or TVCUT_FISTA (one step launch, the projection-mode scan and a
+ * one-thread momentum launch per iteration; the momentum sequence is kept on
+ * the device, so replays continue it).  TVCUT_BCD is refused (INVALID). */
 typedef struct tvcut_batch_ctx* tvcut_batch_t;
 
 /* G grids; dims holds G pairs {H_g, W_g} (1 <= H_g, W_g <= 2^20).  Allocates
- * about 8 arrays of sum_g H_g W_g values.  Errors: INVALID, OOM, CUDA. */
+ * about 8 arrays of sum_g H_g W_g values (10 for FISTA).  Errors: INVALID,
+ * OOM, CUDA. */
 tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvcut_params* p,
                                 void* cuda_stream, tvcut_batch_t* out);
 void tvcut_batch_destroy(tvcut_batch_t b);

@@ -7,6 +7,11 @@
 //             grid and axis, longest chains first) from an atomic counter;
 //   update -- the AAR/AP update of every vertex of every grid (Eq. 3 with
 //             Eq. dualA, or Sec. 4.2) over 32x32 tiles, grid-stride.
+// FISTA (Sec. 4.1, smooth dual) runs the extrapolation and gradient step
+// first (tiles), then the scan in projection mode, which writes the new
+// iterate over the previous one; the two buffers swap roles every iteration
+// and the momentum sequence t lives in device memory, so a captured graph
+// replays correctly.
 // A whole call (its iterations and the closing check) is captured once into
 // a CUDA graph per iteration count and replayed.  Per grid, the check sums
 // row-chunk partials in a fixed order (reproducible) and picks the best of
@@ -20,6 +25,7 @@
 
 #include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "taut_string.cuh"
@@ -60,8 +66,11 @@ struct BatchArgs {
     int G;
     T* s0;            // axis-0 block states (natural)
     T* s1;            // axis-1 block states (transposed)
-    T* x0;            // axis-0 prox outputs
+    T* x0;            // axis-0 prox outputs (FISTA: the points v to project)
     T* x1;
+    T* p0;            // FISTA: previous iterate (natural / transposed)
+    T* p1;
+    double* mom;      // FISTA: t_{k-1}, t_k
     const T* w;
     const T* a0;
     const T* a1;
@@ -79,7 +88,7 @@ struct BatchArgs {
     const T* best_level;      // per grid (labels pass)
 };
 
-template <typename T, bool PRED>
+template <typename T, bool PRED, bool SHADOW>
 __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
 {
     __shared__ int item_s;
@@ -94,15 +103,78 @@ __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
             const GridDesc D = A.grids[I.g];
             const int c = I.c0 + t;
             const int64_t b = D.off + c;
+            // prox of s into x, or (SHADOW, FISTA) projection of v = x into p
+            const T* in = SHADOW ? (I.axis == 0 ? A.x0 : A.x1) : (I.axis == 0 ? A.s0 : A.s1);
+            T* out = SHADOW ? (I.axis == 0 ? A.p0 : A.p1) : (I.axis == 0 ? A.x0 : A.x1);
             if (I.axis == 0) {        // column c: H elements, stride W (natural)
-                if (PRED) scan_chain_predicated<T>(D.H, A.s0 + b, A.a0 + D.aoff0 + c, A.x0 + b, D.W);
-                else scan_chain<T>(D.H, A.s0 + b, A.a0 + D.aoff0 + c, A.x0 + b, D.W);
+                if (PRED) scan_chain_predicated<T, SHADOW>(D.H, in + b, A.a0 + D.aoff0 + c, out + b, D.W);
+                else scan_chain<T, SHADOW>(D.H, in + b, A.a0 + D.aoff0 + c, out + b, D.W);
             } else {                  // row c: W elements, stride H (transposed)
-                if (PRED) scan_chain_predicated<T>(D.W, A.s1 + b, A.a1 + D.aoff1 + c, A.x1 + b, D.H);
-                else scan_chain<T>(D.W, A.s1 + b, A.a1 + D.aoff1 + c, A.x1 + b, D.H);
+                if (PRED) scan_chain_predicated<T, SHADOW>(D.W, in + b, A.a1 + D.aoff1 + c, out + b, D.H);
+                else scan_chain<T, SHADOW>(D.W, in + b, A.a1 + D.aoff1 + c, out + b, D.H);
             }
         }
     }
+}
+
+// FISTA step on every vertex of every grid: u_k = y_k + beta (y_k - p_k),
+// v_k = u_k + (w - u_0 - u_1) / 2 into x_k (the block of axis 1 transposed);
+// beta = (t_{k-1} - 1) / t_k from device memory.  EVAL instead writes the
+// primal x = w - y_0 - y_1 for the check.
+template <typename T, bool EVAL>
+__global__ void __launch_bounds__(256) batch_fista_kernel(BatchArgs<T> A)
+{
+    __shared__ T sy[32][33];
+    __shared__ T sp[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const T beta = EVAL ? T(0) : (T)((A.mom[0] - 1.0) / A.mom[1]);
+    for (int ti = blockIdx.x; ti < A.ntiles; ti += gridDim.x) {
+        const Tile tile = A.tiles[ti];
+        const GridDesc D = A.grids[tile.g];
+        const int64_t H = D.H, W = D.W;
+        __syncthreads();
+#pragma unroll
+        for (int cc = ty; cc < 32; cc += 8) {
+            const int64_t c = tile.c0 + cc, r = tile.r0 + tx;
+            if (c < W && r < H) {
+                sy[cc][tx] = A.s1[D.off + c * H + r];
+                if (!EVAL) sp[cc][tx] = A.p1[D.off + c * H + r];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int64_t r = tile.r0 + rr, c = tile.c0 + tx;
+            if (r >= H || c >= W) continue;
+            const int64_t g = D.off + r * W + c;
+            const T wg = A.w[g];
+            const T y0 = A.s0[g], y1 = sy[tx][rr];
+            if (EVAL) {
+                A.xout[g] = (wg - y0) - y1;           // as the single-grid path
+                continue;
+            }
+            const T u0 = y0 + beta * (y0 - A.p0[g]);
+            const T u1 = y1 + beta * (y1 - sp[tx][rr]);
+            const T corr = (wg - (u0 + u1)) / T(2);
+            A.x0[g] = u0 + corr;
+            sy[tx][rr] = u1 + corr;
+        }
+        if (EVAL) continue;
+        __syncthreads();
+#pragma unroll
+        for (int cc = ty; cc < 32; cc += 8) {
+            const int64_t c = tile.c0 + cc, r = tile.r0 + tx;
+            if (c < W && r < H) A.x1[D.off + c * H + r] = sy[cc][tx];
+        }
+    }
+}
+
+// t_{k-1} <- t_k, t_k <- (1 + sqrt(1 + 4 t_k^2)) / 2 (one thread)
+__global__ void batch_momentum_kernel(double* mom)
+{
+    const double t = mom[1];
+    mom[0] = t;
+    mom[1] = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
 }
 
 template <typename T, int MODE>
@@ -341,6 +413,9 @@ struct tvcut_batch_ctx {
     int* d_first_row = nullptr;
     int* d_counter = nullptr;
     void *s0 = nullptr, *s1 = nullptr, *x0 = nullptr, *x1 = nullptr, *w = nullptr, *a0 = nullptr, *a1 = nullptr;
+    void *p0 = nullptr, *p1 = nullptr;   // FISTA: the other iterate buffers
+    double* mom = nullptr;               // FISTA: t_{k-1}, t_k
+    bool flip = false;                   // FISTA: the current iterate is in p0/p1
     void* xout = nullptr;
     void* stage = nullptr;            // staging of one grid's host input (max grid bytes x 8)
     uint8_t* labels = nullptr;
@@ -371,6 +446,7 @@ struct tvcut_batch_ctx {
     // graph cache
     cudaGraphExec_t graph = nullptr;
     int64_t graph_iters = -1;
+    bool graph_flip = false;
     std::string err;
 };
 
@@ -406,7 +482,7 @@ extern "C" void tvcut_batch_destroy(tvcut_batch_t b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void* ptrs[] = {b->d_grids, b->d_items, b->d_tiles, b->d_rows, b->d_first_row, b->d_counter, b->s0, b->s1,
                     b->x0, b->x1, b->w, b->a0, b->a1, b->xout, b->stage, b->labels, b->levels, b->best,
-                    b->partials, b->lpartials, b->gsum, b->glev, b->d_flags, b->d_absmax};
+                    b->partials, b->lpartials, b->gsum, b->glev, b->d_flags, b->d_absmax, b->p0, b->p1, b->mom};
     for (void* q : ptrs) cudaFree(q);
     delete b;
 }
@@ -420,7 +496,7 @@ extern "C" tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvc
     tvcut_params prm;
     tvcut_default_params(&prm);
     if (p) prm = *p;
-    if ((prm.algo != TVCUT_AAR && prm.algo != TVCUT_AP) || (prm.iterate_dtype != TVCUT_F32 && prm.iterate_dtype != TVCUT_F64) ||
+    if ((prm.algo != TVCUT_AAR && prm.algo != TVCUT_AP && prm.algo != TVCUT_FISTA) || (prm.iterate_dtype != TVCUT_F32 && prm.iterate_dtype != TVCUT_F64) ||
         prm.level_sets < 0 || 2 * prm.level_sets + 1 > kMaxLevels || prm.threshold != prm.threshold)
         return bfail(nullptr, TVCUT_ERR_INVALID, "tvcut_batch_create: bad params");
     tvcut_batch_t b = new tvcut_batch_ctx();
@@ -486,6 +562,11 @@ extern "C" tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvc
     A(&b->a0, es * b->na0);
     A(&b->a1, es * b->na1);
     A(&b->xout, es * b->n);
+    if (prm.algo == TVCUT_FISTA) {
+        A(&b->p0, es * b->n);
+        A(&b->p1, es * b->n);
+        A((void**)&b->mom, 2 * sizeof(double));
+    }
     A(&b->stage, 8 * (size_t)maxn);
     A((void**)&b->labels, (size_t)b->n);
     A(&b->levels, es * (size_t)G * kMaxLevels);
@@ -541,6 +622,13 @@ static BatchArgs<T> args_of(tvcut_batch_t b)
     A.s1 = (T*)b->s1;
     A.x0 = (T*)b->x0;
     A.x1 = (T*)b->x1;
+    A.p0 = (T*)b->p0;
+    A.p1 = (T*)b->p1;
+    A.mom = b->mom;
+    if (b->flip) {                       // FISTA: the current iterate is in p
+        std::swap(A.s0, A.p0);
+        std::swap(A.s1, A.p1);
+    }
     A.w = (const T*)b->w;
     A.a0 = (const T*)b->a0;
     A.a1 = (const T*)b->a1;
@@ -679,6 +767,14 @@ static tvcut_status breset(tvcut_batch_t b)
         BCK(b, cudaMemsetAsync(b->s0, 0, (size_t)b->esize * b->n, b->stream), "tvcut_batch_reset");
         BCK(b, cudaMemsetAsync(b->s1, 0, (size_t)b->esize * b->n, b->stream), "tvcut_batch_reset");
     }
+    if (b->p.algo == TVCUT_FISTA) {      // y_prev = y = 0, t_0 = t_1 = 1
+        static const double one[2] = {1.0, 1.0};
+        BCK(b, cudaMemsetAsync(b->p0, 0, (size_t)b->esize * b->n, b->stream), "tvcut_batch_reset");
+        BCK(b, cudaMemsetAsync(b->p1, 0, (size_t)b->esize * b->n, b->stream), "tvcut_batch_reset");
+        BCK(b, cudaMemcpyAsync(b->mom, one, sizeof(one), cudaMemcpyHostToDevice, b->stream), "tvcut_batch_reset");
+        BCK(b, cudaStreamSynchronize(b->stream), "tvcut_batch_reset");
+        b->flip = false;
+    }
     b->iters = 0;
     b->checked = false;
     return TVCUT_OK;
@@ -697,14 +793,29 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
 {
     BatchArgs<T> A = args_of<T>(b);
     const bool aar = b->p.algo == TVCUT_AAR;
+    const bool fista = b->p.algo == TVCUT_FISTA;
+    const unsigned scan_grid = (unsigned)(b->sms * b->scan_ctas_per_sm);
     for (int64_t it = 0; it < iters; ++it) {
         A.check = it == iters - 1;
-        cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
-        if (e != cudaSuccess) return e;
-        if (b->scan_predicated) batch_scan_kernel<T, true><<<b->sms * b->scan_ctas_per_sm, b->scan_threads, 0, b->stream>>>(A);
-        else batch_scan_kernel<T, false><<<b->sms * b->scan_ctas_per_sm, b->scan_threads, 0, b->stream>>>(A);
-        if (aar) batch_update_kernel<T, UPD_AAR><<<b->sms * 16, 256, 0, b->stream>>>(A);
-        else batch_update_kernel<T, UPD_AP><<<b->sms * 16, 256, 0, b->stream>>>(A);
+        cudaError_t e = cudaSuccess;
+        if (fista) {
+            batch_fista_kernel<T, false><<<b->sms * 16, 256, 0, b->stream>>>(A);
+            e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+            if (e != cudaSuccess) return e;
+            if (b->scan_predicated) batch_scan_kernel<T, true, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else batch_scan_kernel<T, false, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            batch_momentum_kernel<<<1, 1, 0, b->stream>>>(b->mom);
+            std::swap(A.s0, A.p0);                // the new iterate is where the scan wrote
+            std::swap(A.s1, A.p1);
+            if (A.check) batch_fista_kernel<T, true><<<b->sms * 16, 256, 0, b->stream>>>(A);
+        } else {
+            e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+            if (e != cudaSuccess) return e;
+            if (b->scan_predicated) batch_scan_kernel<T, true, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else batch_scan_kernel<T, false, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            if (aar) batch_update_kernel<T, UPD_AAR><<<b->sms * 16, 256, 0, b->stream>>>(A);
+            else batch_update_kernel<T, UPD_AP><<<b->sms * 16, 256, 0, b->stream>>>(A);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -745,7 +856,7 @@ static tvcut_status biterate(tvcut_batch_t b, int64_t iters, tvcut_stats* out)
 {
     tvcut_status st = prepare_levels<T>(b);
     if (st != TVCUT_OK) return st;
-    if (b->graph_iters != iters || !b->graph) {
+    if (b->graph_iters != iters || b->graph_flip != b->flip || !b->graph) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
@@ -771,9 +882,11 @@ static tvcut_status biterate(tvcut_batch_t b, int64_t iters, tvcut_stats* out)
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
         b->graph_iters = iters;
+        b->graph_flip = b->flip;
     }
     BCK(b, cudaGraphLaunch(b->graph, b->stream), "tvcut_batch_iterate");
     b->iters += iters;
+    if (b->p.algo == TVCUT_FISTA && (iters & 1)) b->flip = !b->flip;
     BCK(b, cudaMemcpyAsync(b->h_gsum.data(), b->gsum, sizeof(CheckPartial) * b->G, cudaMemcpyDeviceToHost, b->stream),
         "tvcut_batch_iterate");
     if (b->L > 0)
@@ -859,8 +972,9 @@ static tvcut_status bget_state(tvcut_batch_t b, int g, void* s, int space)
     const GridDesc& D = b->grids[g];
     const int64_t n = (int64_t)D.H * D.W;
     const cudaMemcpyKind k = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    BCK(b, cudaMemcpyAsync(s, (T*)b->s0 + D.off, sizeof(T) * n, k, b->stream), "tvcut_batch_get_state");
-    BCK(b, launch_transpose<T>((T*)b->s1 + D.off, (T*)b->stage, D.W, D.H, b->stream), "tvcut_batch_get_state");
+    const BatchArgs<T> A = args_of<T>(b);            // the current iterate (FISTA: either buffer)
+    BCK(b, cudaMemcpyAsync(s, A.s0 + D.off, sizeof(T) * n, k, b->stream), "tvcut_batch_get_state");
+    BCK(b, launch_transpose<T>(A.s1 + D.off, (T*)b->stage, D.W, D.H, b->stream), "tvcut_batch_get_state");
     BCK(b, cudaMemcpyAsync((T*)s + n, b->stage, sizeof(T) * n, k, b->stream), "tvcut_batch_get_state");
     BCK(b, cudaStreamSynchronize(b->stream), "tvcut_batch_get_state");
     return TVCUT_OK;
@@ -899,8 +1013,8 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
                 for (int rep = 0; rep < 3; ++rep) {
                     BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream), "autotune");
                     BCK(b, cudaEventRecord(e0, b->stream), "autotune");
-                    if (pv) batch_scan_kernel<T, true><<<b->sms * q, t, 0, b->stream>>>(A);
-                    else batch_scan_kernel<T, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    if (pv) batch_scan_kernel<T, true, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    else batch_scan_kernel<T, false, false><<<b->sms * q, t, 0, b->stream>>>(A);
                     BCK(b, cudaGetLastError(), "autotune");
                     BCK(b, cudaEventRecord(e1, b->stream), "autotune");
                     BCK(b, cudaEventSynchronize(e1), "autotune");

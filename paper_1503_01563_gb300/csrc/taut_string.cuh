@@ -106,7 +106,7 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
 // that the lanes of a warp, which bend, clamp and restart at different
 // elements, stay on one instruction stream: every candidate update is
 // computed and the valid one selected.
-template <typename T>
+template <typename T, bool SHADOW = false>
 __device__ __forceinline__ void scan_chain_predicated(int m, const T* __restrict__ v, const T* __restrict__ a,
                                            T* __restrict__ x, int64_t stride)
 {
@@ -128,7 +128,7 @@ __device__ __forceinline__ void scan_chain_predicated(int m, const T* __restrict
             const int e = bhi ? ih : il;
             const T t = bhi ? th : tl;
             u0 = bhi ? ah : -al;
-            for (int j = s; j <= e; ++j, px += stride) *px = t;
+            for (int j = s; j <= e; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - t : t;
             s = e + 1;
             if (s < i) {                         // rescan from the bend
                 i = s;
@@ -152,7 +152,7 @@ __device__ __forceinline__ void scan_chain_predicated(int m, const T* __restrict
         ah = (start || ch) ? Ai : ah;
         al = (start || cl) ? Ai : al;
         if (i == m - 1) {
-            for (int j = s; j <= m - 1; ++j, px += stride) *px = th;
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - th : th;
             break;
         }
         ++i;

@@ -25,7 +25,7 @@ def problems(seed0=100):
     return [inputs.uniform_grid(d, seed0 + i) for i, d in enumerate(DIMS)]
 
 
-@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("algo", [0, 1, 3])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_batch_matches_single_grid_and_oracle(tv, orc, algo, dtype):
     code = tv.F64 if dtype == "f64" else tv.F32
@@ -48,9 +48,10 @@ def test_batch_matches_single_grid_and_oracle(tv, orc, algo, dtype):
     b.close()
 
 
-def test_batch_exact_cuts(tv, orc):
+@pytest.mark.parametrize("algo", [0, 3])
+def test_batch_exact_cuts(tv, orc, algo):
     probs = problems(200)
-    b = tv.Batch(DIMS, dtype=tv.F64)
+    b = tv.Batch(DIMS, algo=algo, dtype=tv.F64)
     for g, (w, a) in enumerate(probs):
         b.set_problem(g, w, a)
     b.reset()
@@ -64,11 +65,15 @@ def test_batch_exact_cuts(tv, orc):
     b.close()
 
 
-def test_batch_graph_replay_deterministic(tv):
+@pytest.mark.parametrize("algo", [0, 3])
+def test_batch_graph_replay_deterministic(tv, orc, algo):
+    """Replays of one captured graph (3 x 4 iterations) give identical results
+    run to run; for FISTA, 3 x 3 iterations (an odd count alternates the roles
+    of the two iterate buffers between calls) match the oracle's 9 steps."""
     probs = problems(300)
     runs = []
     for _ in range(2):
-        b = tv.Batch(DIMS, dtype=tv.F32)
+        b = tv.Batch(DIMS, algo=algo, dtype=tv.F32)
         for g, (w, a) in enumerate(probs):
             b.set_problem(g, w, a)
         b.reset()
@@ -79,6 +84,17 @@ def test_batch_graph_replay_deterministic(tv):
     for s1, s2 in zip(runs[0][0], runs[1][0]):
         np.testing.assert_array_equal(s1, s2)
     assert runs[0][1] == runs[1][1]
+    if algo == 3:
+        b = tv.Batch(DIMS, algo=algo, dtype=tv.F32)
+        for g, (w, a) in enumerate(probs):
+            b.set_problem(g, w, a)
+        b.reset()
+        for _ in range(3):
+            b.iterate(3)
+        for g, (w, a) in enumerate(probs):
+            ref, _ = orc.iterate(3, w, a, orc.cold_state(3, w), 9)
+            assert np.abs(b.state(g) - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+        b.close()
 
 
 def test_batch_autotune_keeps_results(tv):
@@ -100,6 +116,8 @@ def test_batch_autotune_keeps_results(tv):
 def test_batch_errors(tv):
     with pytest.raises(tv.TvcutError):
         tv.Batch([(0, 5)])
+    with pytest.raises(tv.TvcutError):
+        tv.Batch([(4, 4)], algo=2)                # BCD is single-grid only
     b = tv.Batch([(4, 4), (3, 5)])
     w, a = inputs.uniform_grid((4, 4), 1)
     b.set_problem(0, w, a)

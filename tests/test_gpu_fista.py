@@ -98,10 +98,7 @@ def test_fista_set_state_restarts_momentum(tv, orc):
     s2.close()
 
 
-def test_fista_rejected_where_not_built(tv):
+def test_fista_rejected_with_fused_sweeps(tv):
     with pytest.raises(tv.TvcutError) as e:
         tv.Solver((8, 8), algo=FISTA, mapping=3)
-    assert e.value.code == tv.ERR_INVALID
-    with pytest.raises(tv.TvcutError) as e:
-        tv.Batch([(8, 8)], algo=FISTA)
     assert e.value.code == tv.ERR_INVALID
