@@ -236,6 +236,7 @@ struct tvcut_unet_ctx {
     std::vector<Act> acts;
     float* out16 = nullptr;                      // N x H x W x 16 FP32 output
     float* loss = nullptr;
+    int engine = 0;                              // convolutions: 0 tcgen05 where supported, 1 mma.sync
     std::string err;
 };
 
@@ -410,6 +411,17 @@ extern "C" tvcut_status tvcut_unet_resize(tvcut_unet_t u, int N, int H, int W)
     return alloc_acts(u, N, H, W);
 }
 
+// A 3x3 convolution: the tcgen05 kernel when the shape allows it (engine 0),
+// else the mma.sync kernel.
+static cudaError_t launch_conv(const ConvArgs& A, int engine, cudaStream_t s)
+{
+    if (engine != 1 && conv_tc_supported(A)) return launch_conv3x3_tc(A, s);
+    const int64_t P = (int64_t)A.N * A.H * A.W;
+    dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((A.Cout + BN - 1) / BN));
+    conv3x3_fwd_kernel<<<grid, FTHREADS, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 static tvcut_status run_conv(tvcut_unet_t u, int ci, const Act& in, Act& out, const bf16* wt, bool bias)
 {
     const Conv& c = u->convs[ci];
@@ -427,10 +439,7 @@ static tvcut_status run_conv(tvcut_unet_t u, int ci, const Act& in, Act& out, co
     A.Cout = c.cout;
     A.CoutStride = c.cout;
     A.relu = c.relu;
-    const int64_t P = (int64_t)A.N * A.H * A.W;
-    dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((c.cout + BN - 1) / BN));
-    conv3x3_fwd_kernel<<<grid, FTHREADS, 0, u->stream>>>(A);
-    UCK(u, cudaGetLastError(), "conv forward");
+    UCK(u, launch_conv(A, u->engine, u->stream), "conv forward");
     return TVCUT_OK;
 }
 
@@ -540,8 +549,7 @@ static tvcut_status conv_backward(tvcut_unet_t u, int ci, const Act& in, const A
         A.Cout = c.cin;
         A.CoutStride = c.cin;
         A.relu = 0;
-        dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((c.cin + BN - 1) / BN));
-        conv3x3_fwd_kernel<<<grid, FTHREADS, 0, u->stream>>>(A);
+        UCK(u, launch_conv(A, u->engine, u->stream), "conv backward");
     }
     UCK(u, cudaGetLastError(), "conv backward");
     return TVCUT_OK;
@@ -676,8 +684,15 @@ extern "C" tvcut_status tvcut_unet_set_params(tvcut_unet_t u, const float* src)
 extern "C" tvcut_status tvcut_conv3x3_bf16(const void* in, const void* wt, const float* bias, void* out, int N, int H,
                                            int W, int Cin, int Cout, int relu, void* stream)
 {
+    return tvcut_conv3x3_bf16_ex(in, wt, bias, out, N, H, W, Cin, Cout, relu, 0, stream);
+}
+
+extern "C" tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, const float* bias, void* out, int N,
+                                              int H, int W, int Cin, int Cout, int relu, int engine, void* stream)
+{
     if (!in || !wt || !out || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 16 || Cin < 16 || Cout < 16)
         return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16: bad arguments (channels multiples of 16)");
+    if (engine < 0 || engine > 2) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16_ex: engine must be 0, 1 or 2");
     ConvArgs A;
     A.in = (const bf16*)in;
     A.wt = (const bf16*)wt;
@@ -692,11 +707,13 @@ extern "C" tvcut_status tvcut_conv3x3_bf16(const void* in, const void* wt, const
     A.Cout = Cout;
     A.CoutStride = Cout;
     A.relu = relu;
-    const int64_t P = (int64_t)N * H * W;
-    dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((Cout + BN - 1) / BN));
-    conv3x3_fwd_kernel<<<grid, FTHREADS, 0, (cudaStream_t)stream>>>(A);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return ufail(nullptr, TVCUT_ERR_CUDA, cudaGetErrorString(e));
+    if (engine == 2 && !conv_tc_supported(A))
+        return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16_ex: shape not supported by the tcgen05 kernel");
+    cudaError_t e = launch_conv(A, engine == 1 ? 1 : 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ufail(nullptr, TVCUT_ERR_CUDA, cudaGetErrorString(e));
+    }
     return TVCUT_OK;
 }
 
@@ -722,4 +739,17 @@ extern "C" tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dou
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ufail(nullptr, TVCUT_ERR_CUDA, cudaGetErrorString(e));
     return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine)
+{
+    if (!u) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_unet_set_engine: NULL handle");
+    if (engine != 0 && engine != 1) return ufail(u, TVCUT_ERR_INVALID, "tvcut_unet_set_engine: engine must be 0 or 1");
+    u->engine = engine;
+    return TVCUT_OK;
+}
+
+extern "C" int tvcut_conv_tc_error(void)
+{
+    return conv_tc_take_error();
 }

@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "conv_args.cuh"
+
 namespace tvcut {
 namespace nn {
 
@@ -48,16 +50,7 @@ __device__ __forceinline__ void warp_tile_mma(const __nv_bfloat16 (*As)[SROW], c
     }
 }
 
-struct ConvArgs {
-    const __nv_bfloat16* in;    // N x H x W x Cin
-    const __nv_bfloat16* wt;    // 9 x Cout x Cin
-    const float* bias;          // Cout or nullptr
-    __nv_bfloat16* out;         // N x H x W x CoutStride (channels >= Cout untouched)
-    float* out_f32;             // optional FP32 copy (N x H x W x Cout) or nullptr
-    const __nv_bfloat16* mask;  // optional: out *= (mask > 0), same layout as out
-    int N, H, W, Cin, Cout, CoutStride;
-    int relu;
-};
+
 
 // out[p][co] = act(bias[co] + sum_k sum_ci in[p + off_k][ci] * wt[k][co][ci])
 //

@@ -58,6 +58,85 @@ def test_conv_forward_and_wgrad(tv, shape):
     assert rel(dw.cpu().numpy(), W.grad.numpy()) < 2e-2
 
 
+TC_SHAPES = [(1, 16, 128, 16, 32), (2, 16, 64, 32, 16), (1, 8, 256, 64, 128), (1, 4, 128, 128, 256),
+             (1, 16, 32, 256, 64), (3, 2, 128, 16, 16), (1, 64, 16, 64, 48)]
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES)
+@pytest.mark.parametrize("relu", [0, 1])
+def test_conv_tcgen05(tv, shape, relu):
+    """The tcgen05 kernel (engine 2) against the CPU reference and against the
+    mma.sync kernel (engine 1): same BF16 inputs, FP32 accumulation in a
+    different order, so the BF16 outputs differ by rounding only."""
+    from oracle import unet_ref
+    n, h, w, ci, co = shape
+    rng = np.random.default_rng(sum(shape) + relu)
+    x = bf16_round(rng.normal(size=(n, h, w, ci)))
+    wk = bf16_round(rng.normal(size=(9, co, ci)) * (0.6 / np.sqrt(ci)))
+    b = rng.normal(size=co).astype(np.float32)
+    xd = torch.tensor(x).to(torch.bfloat16).cuda()
+    wd = torch.tensor(wk).to(torch.bfloat16).cuda()
+    bd = torch.tensor(b).cuda()
+    outs = []
+    for engine in (2, 1):
+        out = torch.full((n, h, w, co), 7.0, dtype=torch.bfloat16, device="cuda")
+        code = tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(),
+                                              n, h, w, ci, co, relu, engine, None)
+        assert code == tv.OK
+        torch.cuda.synchronize()
+        outs.append(out.float().cpu().numpy())
+    assert tv.lib().tvcut_conv_tc_error() == 0
+    Wt = torch.tensor(wk).reshape(3, 3, co, ci).permute(2, 3, 0, 1)
+    xt = torch.tensor(x).permute(0, 3, 1, 2)
+    ref = unet_ref.F.conv2d(xt, Wt, torch.tensor(b), padding=1).permute(0, 2, 3, 1)
+    if relu:
+        ref = torch.relu(ref)
+    ref = ref.numpy()
+    assert rel(outs[0], ref) < 1e-2
+    assert rel(outs[0], outs[1]) < 1e-2
+    # rounding only: no output differs by more than a few BF16 steps of its magnitude
+    assert np.all(np.abs(outs[0] - outs[1]) <= 2 ** -6 * np.maximum(np.abs(outs[1]), 1.0))
+
+
+def test_conv_tcgen05_rejects_other_shapes(tv):
+    x = torch.zeros((2, 9, 13, 32), dtype=torch.bfloat16, device="cuda")
+    wk = torch.zeros((9, 16, 32), dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros((2, 9, 13, 16), dtype=torch.bfloat16, device="cuda")
+    code = tv.lib().tvcut_conv3x3_bf16_ex(x.data_ptr(), wk.data_ptr(), None, out.data_ptr(), 2, 9, 13, 32, 16, 0, 2,
+                                          None)
+    assert code == tv.ERR_INVALID
+    # engine 0 takes the mma.sync kernel for it
+    code = tv.lib().tvcut_conv3x3_bf16_ex(x.data_ptr(), wk.data_ptr(), None, out.data_ptr(), 2, 9, 13, 32, 16, 0, 0,
+                                          None)
+    assert code == tv.OK
+
+
+def test_network_engines_agree(tv):
+    """128 x 128 images: every layer's shape goes to the tcgen05 kernel
+    (engine 0); the same network on the mma.sync kernels (engine 1) and the
+    CPU oracle agree with it."""
+    from oracle import unet_ref
+    base, n, h, w = 32, 2, 128, 128
+    net = tv.UNet(base=base, batch=n, H=h, W=w, seed=5)
+    rng = np.random.default_rng(6)
+    x = torch.tensor(rng.normal(size=(n, h, w, 3)).astype(np.float32)).cuda()
+    t = torch.tensor(rng.normal(size=(n, h, w, 2)).astype(np.float32)).cuda()
+    res = []
+    for engine in (0, 1):
+        net.set_engine(engine)
+        out = net.forward(x).cpu().numpy()
+        loss = net.backward(t)
+        res.append((out, loss, net.params(which=1)))
+    assert tv.lib().tvcut_conv_tc_error() == 0
+    assert rel(res[0][0], res[1][0]) < 1e-2
+    assert abs(res[0][1] - res[1][1]) < 1e-2 * res[1][1]
+    assert rel(res[0][2], res[1][2]) < 5e-2
+    theta_bf = bf16_round(net.params())
+    ref_loss, _, ref_out = unet_ref.loss_and_grad(theta_bf, bf16_round(x.cpu().numpy()), t.cpu().numpy(), base)
+    assert rel(res[0][0], ref_out) < 5e-2
+    net.close()
+
+
 def test_network_forward_backward(tv):
     from oracle import unet_ref
     base, n, h, w = 32, 2, 32, 24
