@@ -40,7 +40,14 @@ WORKLOADS = {
     # learned warm start: U-Net (4 levels, 32 channels) trained on solver-generated 128^2 problems,
     # evaluated on held-out 2048^2 problems (w ~ U{-50..50}, a ~ U{1..20}), cold vs warm
     "warm2048": dict(dims=(2048, 2048), seed=999, cap=3000, train_n=4096, train_hw=128, train_steps=1500),
+    # the warm-start network's inference alone: U-Net (4 levels, 32 channels) on one 2048^2 input,
+    # randomly initialised weights; its 3x3 convolutions are the one dense contraction of the path
+    "unet2048": dict(dims=(2048, 2048), seed=21, base=32),
 }
+# (level, Cin, Cout) of the U-Net's 18 convolutions in forward order (level l: resolution / 2^l)
+UNET_CONVS = [(0, 16, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 128), (2, 128, 128), (3, 128, 256),
+              (3, 256, 256), (2, 256, 128), (2, 256, 128), (2, 128, 128), (1, 128, 64), (1, 128, 64), (1, 64, 64),
+              (0, 64, 32), (0, 64, 32), (0, 32, 32), (0, 32, 16)]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -187,6 +194,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "unet2048":
+        return run_reference_unet(args)
     import oracle
     oracle.build()
     w, a = make_problem(args.workload)
@@ -211,6 +220,37 @@ def run_reference(args):
            "cpu_baseline": {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
                             "sample": f"{args.steps} whole-grid FP64 {args.algo.upper()} iterations"},
            "e2e": {"value": value, "unit": "Mvertex-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_reference_unet(args):
+    """The oracle's U-Net forward (PyTorch CPU FP32) on 512x512 crops of the
+    2048^2 input, reported in TFLOP/s."""
+    import torch
+    import oracle.unet_ref as unet_ref
+    wl = WORKLOADS["unet2048"]
+    H, W = wl["dims"]
+    hs = 512
+    flops = sum(2.0 * (hs >> l) * (hs >> l) * 9 * ci * co for l, ci, co in UNET_CONVS)
+    g = np.random.default_rng(wl["seed"])
+    x = torch.from_numpy(g.normal(size=(1, hs, hs, 3)).astype(np.float32))
+    theta = torch.from_numpy(g.normal(size=unet_ref.num_params(wl["base"])).astype(np.float32) * 0.05)
+    with torch.no_grad():
+        for _ in range(args.warmup):
+            unet_ref.forward(theta, x, wl["base"])
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            unet_ref.forward(theta, x, wl["base"])
+        dt = (time.perf_counter() - t0) / args.steps
+    value = flops / dt / 1e12
+    out = {"impl": "reference", "metric": "TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "unet2048", "dims": [H, W], "step": f"oracle forward on a {hs}x{hs} crop"},
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                            "sample": f"{args.steps} oracle forwards on {hs}x{hs} crops"},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -491,6 +531,102 @@ def run_warm(args):
     return 0
 
 
+def run_unet(args):
+    """U-Net inference at 2048^2: TFLOP/s of the forward pass (its 18 3x3
+    convolutions as implicit GEMMs; pooling, upsampling and concatenation
+    counted as zero flops) with the tcgen05 convolutions, beside the same
+    network on the mma.sync kernels; end to end with a host input and output."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank != 0:
+        return 0                                   # single-GPU workload: extra ranks idle
+    torch.cuda.set_device(local)
+    from paper_1503_01563_gb300 import tvcut
+    wl = WORKLOADS["unet2048"]
+    H = W = args.unet_hw
+    flops = sum(2.0 * (H >> l) * (W >> l) * 9 * ci * co for l, ci, co in UNET_CONVS)
+    g = np.random.default_rng(wl["seed"])
+    x = g.normal(size=(1, H, W, 3)).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    net = tvcut.UNet(base=wl["base"], batch=1, H=H, W=W, seed=wl["seed"], stream=stream.cuda_stream)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty((1, H, W, 2), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    clk = None
+    for engine in (1, 0):                          # the timed line is engine 0 (tcgen05)
+        net.set_engine(engine)
+        for _ in range(args.warmup):
+            net.forward(xd, out)
+        torch.cuda.synchronize()
+        if engine == 0:
+            clocks = ClockSampler(local)
+            clocks.start()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            net.forward(xd, out)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        if engine == 0:
+            clk = clocks.stop()
+        res[engine] = tot / args.steps
+    err = tvcut.lib().tvcut_conv_tc_error()
+    # end to end: pinned host input -> forward -> host output
+    xp = torch.from_numpy(x).pin_memory()
+    op = torch.empty((1, H, W, 2), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd.copy_(xp, non_blocking=True)
+        net.forward(xd, out)
+        op.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    # CPU oracle (PyTorch CPU FP32 forward) on a 256^2 crop, scaled by flops
+    import oracle.unet_ref as unet_ref
+    theta = torch.from_numpy(net.params())
+    hs = 256
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        unet_ref.forward(theta, torch.from_numpy(x[:, :hs, :hs].copy()), wl["base"])
+    t_cpu = time.perf_counter() - t0
+    cpu_flops = flops * (hs * hs) / (H * W)
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak, peak_kind = float(json.load(open(p))["bf16_tflops"]), "measured (burst)"
+    else:
+        peak, peak_kind = 1900.0, "fallback"
+    tf = flops / (res[0] / 1e3) / 1e12
+    out_json = {"metric": "TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res[0], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": "unet2048" if H == 2048 else f"unet{H}", "dims": [H, W],
+                           "network": "U-Net 4 levels, 32 channels",
+                           "weights": "random init", "gflop_per_forward": flops / 1e9,
+                           "step": "one forward pass (all 29 launches)",
+                           "l2": "256 MB buffer written between steps; activations > L2"},
+                "mma_sync_engine": {"ms": res[1], "TFLOP/s": flops / (res[1] / 1e3) / 1e12},
+                "tcgen05_wait_gave_up": bool(err),
+                "roofline": {"bound": "tensor", "kernel": "forward pass (18 tcgen05 convolutions + elementwise)",
+                             "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                             "peak_source": peak_kind, "traffic": None},
+                "cpu_baseline": {"value": cpu_flops / t_cpu / 1e12, "unit": "TFLOP/s",
+                                 "cores": torch.get_num_threads(), "kind": "oracle",
+                                 "sample": f"oracle forward (PyTorch CPU FP32) on a {hs}x{hs} crop ({t_cpu:.2f} s)"},
+                "e2e": {"value": flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(x.nbytes),
+                        "d2h_bytes_per_step": int(H * W * 2 * 4)},
+                "clocks": clk, "gpu_launches": 29 * args.steps}
+    print(json.dumps(out_json), flush=True)
+    net.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -655,6 +791,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="volume256")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--unet-hw", type=int, default=2048,
+                    help="image size of the unet2048 workload (a multiple of 128; smaller for profiling)")
     ap.add_argument("--algo", choices=sorted(ALGOS), default="aar",
                     help="iteration of the volume256/seg1024 workloads: AAR (Eq. 3), AP (Sec. 4.2), BCD or FISTA (Sec. 4.1)")
     args = ap.parse_args()
@@ -664,6 +802,8 @@ def main():
         return run_batch(args)
     if args.workload == "warm2048":
         return run_warm(args)
+    if args.workload == "unet2048":
+        return run_unet(args)
     return run_ours(args)
 
 

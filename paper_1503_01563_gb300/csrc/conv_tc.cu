@@ -311,8 +311,11 @@ static TcShape tc_shape(const ConvArgs& A)
     int nc = 32;
     while (nc < A.Cout) nc <<= 1;
     S.ncols = nc;
+    // a short ring (about 24 KB) so that many CTAs share an SM: on the U-Net's
+    // layers at 256^2 .. 2048^2 that beat deeper pipelines (2.8 ms for the
+    // 15 inference layers against 4.7 ms with a 96 KB ring)
     const int stage = S.a_bytes + S.b_bytes;
-    int st = (96 * 1024) / stage;             // two CTAs per SM
+    int st = (24 * 1024) / stage;
     if (st < 2) st = 2;
     if (st > S.kblocks) st = S.kblocks;
     if (st > 8) st = 8;
