@@ -28,111 +28,176 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-__global__ void input_pack_kernel(const float* in, bf16* x, int64_t P)
+// Elementwise kernels work on 8 channels (16 bytes) per thread: every
+// channel count is a multiple of 16 and every tensor is its own allocation.
+__device__ __forceinline__ void unpack8(const uint4& u, float* f)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P * 16; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i / 16;
-        const int c = (int)(i % 16);
-        x[i] = __float2bfloat16(c < 3 ? in[p * 3 + c] : 0.f);
+    const __nv_bfloat162* h = (const __nv_bfloat162*)&u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
     }
 }
 
+__device__ __forceinline__ uint4 pack8(const float* f)
+{
+    uint4 u;
+    __nv_bfloat162* h = (__nv_bfloat162*)&u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    return u;
+}
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// x[p] = [in[p][0..2], 0 x 13] (one pixel per thread)
+__global__ void input_pack_kernel(const float* in, bf16* x, int64_t P)
+{
+    GRID_STRIDE(p, P) {
+        float f[8] = {in[p * 3], in[p * 3 + 1], in[p * 3 + 2], 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4* o = (uint4*)(x + p * 16);
+        o[0] = pack8(f);
+        o[1] = pack8(z);
+    }
+}
+
+// 2x2 average: out (H/2 x W/2) from in (H x W); one 8-channel group per thread
 __global__ void pool_fwd_kernel(const bf16* in, bf16* out, int N, int H, int W, int C)
 {
-    const int Ho = H / 2, Wo = W / 2;
-    const int64_t total = (int64_t)N * Ho * Wo * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        int64_t q = i / C;
-        const int x = (int)(q % Wo);
-        q /= Wo;
+    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+    const int64_t total = (int64_t)N * Ho * Wo * C8;
+    GRID_STRIDE(i, total) {
+        const int g = (int)(i % C8);
+        const int64_t po = i / C8;
+        const int x = (int)(po % Wo);
+        const int64_t q = po / Wo;
         const int y = (int)(q % Ho);
         const int64_t n = q / Ho;
-        const int64_t b = ((n * H + 2 * y) * W + 2 * x) * C + c;
-        const float s = __bfloat162float(in[b]) + __bfloat162float(in[b + C]) + __bfloat162float(in[b + (int64_t)W * C]) +
-                        __bfloat162float(in[b + (int64_t)W * C + C]);
-        out[i] = __float2bfloat16(0.25f * s);
+        const int64_t b = ((n * H + 2 * y) * W + 2 * x) * C + 8 * g;
+        const int64_t rs = (int64_t)W * C;
+        float f0[8], f1[8], f2[8], f3[8], r[8];
+        unpack8(*(const uint4*)(in + b), f0);
+        unpack8(*(const uint4*)(in + b + C), f1);
+        unpack8(*(const uint4*)(in + b + rs), f2);
+        unpack8(*(const uint4*)(in + b + rs + C), f3);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = 0.25f * (f0[k] + f1[k] + f2[k] + f3[k]);
+        *(uint4*)(out + po * C + 8 * g) = pack8(r);
     }
 }
 
 // g_in (H x W) += g_out (H/2 x W/2) / 4 spread over each 2x2 block
 __global__ void pool_bwd_kernel(const bf16* gout, bf16* gin, int N, int H, int W, int C)
 {
-    const int64_t total = (int64_t)N * H * W * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        int64_t q = i / C;
-        const int x = (int)(q % W);
-        q /= W;
+    const int C8 = C / 8;
+    const int64_t total = (int64_t)N * H * W * C8;
+    GRID_STRIDE(i, total) {
+        const int g = (int)(i % C8);
+        const int64_t p = i / C8;
+        const int x = (int)(p % W);
+        const int64_t q = p / W;
         const int y = (int)(q % H);
         const int64_t n = q / H;
-        const float g = __bfloat162float(gout[((n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
-        gin[i] = __float2bfloat16(__bfloat162float(gin[i]) + 0.25f * g);
+        float a[8], b[8];
+        unpack8(*(const uint4*)(gout + ((n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + 8 * g), b);
+        bf16* d = gin + p * C + 8 * g;
+        unpack8(*(const uint4*)d, a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = a[k] + 0.25f * b[k];
+        *(uint4*)d = pack8(a);
     }
 }
 
 __global__ void up_fwd_kernel(const bf16* in, bf16* out, int N, int H, int W, int C)   // H, W: output size
 {
-    const int64_t total = (int64_t)N * H * W * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        int64_t q = i / C;
-        const int x = (int)(q % W);
-        q /= W;
+    const int C8 = C / 8;
+    const int64_t total = (int64_t)N * H * W * C8;
+    GRID_STRIDE(i, total) {
+        const int g = (int)(i % C8);
+        const int64_t p = i / C8;
+        const int x = (int)(p % W);
+        const int64_t q = p / W;
         const int y = (int)(q % H);
         const int64_t n = q / H;
-        out[i] = in[((n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+        *(uint4*)(out + p * C + 8 * g) =
+            *(const uint4*)(in + ((n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + 8 * g);
     }
 }
 
 __global__ void up_bwd_kernel(const bf16* gout, bf16* gin, int N, int H, int W, int C)  // H, W: input (coarse) size
 {
-    const int64_t total = (int64_t)N * H * W * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        int64_t q = i / C;
-        const int x = (int)(q % W);
-        q /= W;
+    const int C8 = C / 8;
+    const int64_t total = (int64_t)N * H * W * C8;
+    GRID_STRIDE(i, total) {
+        const int g = (int)(i % C8);
+        const int64_t p = i / C8;
+        const int x = (int)(p % W);
+        const int64_t q = p / W;
         const int y = (int)(q % H);
         const int64_t n = q / H;
-        const int64_t b = ((n * 2 * H + 2 * y) * 2 * W + 2 * x) * C + c;
+        const int64_t b = ((n * 2 * H + 2 * y) * 2 * W + 2 * x) * C + 8 * g;
         const int64_t rs = (int64_t)2 * W * C;
-        gin[i] = __float2bfloat16(__bfloat162float(gout[b]) + __bfloat162float(gout[b + C]) +
-                                  __bfloat162float(gout[b + rs]) + __bfloat162float(gout[b + rs + C]));
+        float f0[8], f1[8], f2[8], f3[8], r[8];
+        unpack8(*(const uint4*)(gout + b), f0);
+        unpack8(*(const uint4*)(gout + b + C), f1);
+        unpack8(*(const uint4*)(gout + b + rs), f2);
+        unpack8(*(const uint4*)(gout + b + rs + C), f3);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = f0[k] + f1[k] + f2[k] + f3[k];
+        *(uint4*)(gin + p * C + 8 * g) = pack8(r);
     }
 }
 
 // out = [a | b] along channels
 __global__ void concat_fwd_kernel(const bf16* a, const bf16* b, bf16* out, int64_t P, int Ca, int Cb)
 {
-    const int C = Ca + Cb;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P * C; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i / C;
-        const int c = (int)(i % C);
-        out[i] = c < Ca ? a[p * Ca + c] : b[p * Cb + c - Ca];
+    const int C8 = (Ca + Cb) / 8, A8 = Ca / 8;
+    GRID_STRIDE(i, P * C8) {
+        const int64_t p = i / C8;
+        const int g = (int)(i - p * C8);
+        *(uint4*)(out + 8 * i) = g < A8 ? *(const uint4*)(a + p * Ca + 8 * g)
+                                        : *(const uint4*)(b + p * Cb + 8 * (g - A8));
     }
 }
 
 // ga = g[:, :Ca] (overwrite); gb += g[:, Ca:]
 __global__ void concat_bwd_kernel(const bf16* g, bf16* ga, bf16* gb, int64_t P, int Ca, int Cb)
 {
-    const int C = Ca + Cb;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P * C; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i / C;
-        const int c = (int)(i % C);
-        if (c < Ca) ga[p * Ca + c] = g[i];
-        else {
-            const int64_t j = p * Cb + c - Ca;
-            gb[j] = __float2bfloat16(__bfloat162float(gb[j]) + __bfloat162float(g[i]));
+    const int C8 = (Ca + Cb) / 8, A8 = Ca / 8;
+    GRID_STRIDE(i, P * C8) {
+        const int64_t p = i / C8;
+        const int q = (int)(i - p * C8);
+        const uint4 v = *(const uint4*)(g + 8 * i);
+        if (q < A8) {
+            *(uint4*)(ga + p * Ca + 8 * q) = v;
+        } else {
+            bf16* d = gb + p * Cb + 8 * (q - A8);
+            float x[8], y[8];
+            unpack8(*(const uint4*)d, x);
+            unpack8(v, y);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = x[k] + y[k];
+            *(uint4*)d = pack8(x);
         }
     }
 }
 
-// g *= (y > 0): gradient at a ReLU output -> gradient at its input
+// g *= (y > 0): gradient at a ReLU output -> gradient at its input (n % 8 == 0)
 __global__ void relu_mask_kernel(bf16* g, const bf16* y, int64_t n)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (!(__bfloat162float(y[i]) > 0.f)) g[i] = __float2bfloat16(0.f);
+    GRID_STRIDE(i, n / 8) {
+        float gv[8], yv[8];
+        unpack8(*(const uint4*)(g + 8 * i), gv);
+        unpack8(*(const uint4*)(y + 8 * i), yv);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (!(yv[k] > 0.f)) gv[k] = 0.f;
+        *(uint4*)(g + 8 * i) = pack8(gv);
+    }
 }
 
 // db[c] += sum_p g[p][c]
@@ -450,22 +515,22 @@ static tvcut_status forward(tvcut_unet_t u, const float* in)
     auto& a = u->acts;
     const int N = u->N, H = u->H, W = u->W;
     const int64_t P0 = (int64_t)N * H * W;
-    input_pack_kernel<<<blocks_for(P0 * 16), 256, 0, u->stream>>>(in, a[A_X].y, P0);
+    input_pack_kernel<<<blocks_for(P0), 256, 0, u->stream>>>(in, a[A_X].y, P0);
     const bf16* wf = u->wf;
     auto pool = [&](int i, int o) {
         const int lv = a[i].level;
         const int64_t n = (int64_t)N * (H >> (lv + 1)) * (W >> (lv + 1)) * a[i].c;
-        pool_fwd_kernel<<<blocks_for(n), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
+        pool_fwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
     };
     auto up = [&](int i, int o) {
         const int lv = a[o].level;
         const int64_t n = (int64_t)N * (H >> lv) * (W >> lv) * a[i].c;
-        up_fwd_kernel<<<blocks_for(n), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
+        up_fwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
     };
     auto cat = [&](int x, int s, int o) {
         const int lv = a[o].level;
         const int64_t P = (int64_t)N * (H >> lv) * (W >> lv);
-        concat_fwd_kernel<<<blocks_for(P * a[o].c), 256, 0, u->stream>>>(a[x].y, a[s].y, a[o].y, P, a[x].c, a[s].c);
+        concat_fwd_kernel<<<blocks_for(P * a[o].c / 8), 256, 0, u->stream>>>(a[x].y, a[s].y, a[o].y, P, a[x].c, a[s].c);
     };
     UST(run_conv(u, 0, a[A_X], a[A_E1A], wf, true));
     UST(run_conv(u, 1, a[A_E1A], a[A_E1], wf, true));
@@ -558,7 +623,7 @@ static tvcut_status conv_backward(tvcut_unet_t u, int ci, const Act& in, const A
 static void mask(tvcut_unet_t u, Act& a)
 {
     const int64_t n = (int64_t)u->N * (u->H >> a.level) * (u->W >> a.level) * a.c;
-    relu_mask_kernel<<<blocks_for(n), 256, 0, u->stream>>>(a.g, a.y, n);
+    relu_mask_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a.g, a.y, n);
 }
 
 extern "C" tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target, float* loss_out)
@@ -575,17 +640,17 @@ extern "C" tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target,
     auto pool_b = [&](int o, int i) {       // a[i].g += pool'(a[o].g)
         const int lv = a[i].level;
         const int64_t n = (int64_t)N * (H >> lv) * (W >> lv) * a[i].c;
-        pool_bwd_kernel<<<blocks_for(n), 256, 0, u->stream>>>(a[o].g, a[i].g, N, H >> lv, W >> lv, a[i].c);
+        pool_bwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[o].g, a[i].g, N, H >> lv, W >> lv, a[i].c);
     };
     auto up_b = [&](int o, int i) {         // a[i].g = up'(a[o].g)
         const int lv = a[i].level;
         const int64_t n = (int64_t)N * (H >> lv) * (W >> lv) * a[i].c;
-        up_bwd_kernel<<<blocks_for(n), 256, 0, u->stream>>>(a[o].g, a[i].g, N, H >> lv, W >> lv, a[i].c);
+        up_bwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[o].g, a[i].g, N, H >> lv, W >> lv, a[i].c);
     };
     auto cat_b = [&](int o, int x, int s) { // a[x].g = g[:Cx]; a[s].g += g[Cx:]
         const int lv = a[o].level;
         const int64_t P = (int64_t)N * (H >> lv) * (W >> lv);
-        concat_bwd_kernel<<<blocks_for(P * a[o].c), 256, 0, u->stream>>>(a[o].g, a[x].g, a[s].g, P, a[x].c, a[s].c);
+        concat_bwd_kernel<<<blocks_for(P * a[o].c / 8), 256, 0, u->stream>>>(a[o].g, a[x].g, a[s].g, P, a[x].c, a[s].c);
     };
     // skip tensors receive gradient from the decoder first: clear them
     for (int i : {A_E1, A_E2, A_E3})
