@@ -18,6 +18,10 @@ Minimization" they follow:
 - ``energy``            E(l) = f(l) - w^T l (problem (D))
 - ``bruteforce``        min over all 2^n labellings (problem (D))
 - ``maxflow``           s-t max-flow / min-cut of the energy (Eq. 2 as a cut)
+- ``conn8``             the same for 2D 8-connected grids: edge list, the
+                        zig-zag decomposition (Sec. 3.1, Fig. 2), the four
+                        methods with four blocks, energy, TV, max-flow on an
+                        edge list, brute force
 
 Arrays are numpy; weights are passed per axis in compact layout (the grid's
 shape with dims[k]-1 along axis k).  Parity is pinned for every function by
@@ -81,6 +85,8 @@ def _load():
     lib.oracle_bruteforce.restype = ctypes.c_int
     lib.oracle_maxflow.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
     lib.oracle_maxflow.restype = ctypes.c_int
+    lib.oracle_maxflow_edges.argtypes = [ctypes.c_int, i64, P, i64, P, P, P, P, P, P]
+    lib.oracle_maxflow_edges.restype = ctypes.c_int
     _lib = lib
     return lib
 

@@ -236,6 +236,100 @@ static int64_t push_relabel(graph_t* g, int64_t s, int64_t t)
     return flow;
 }
 
+/* The same graph for an explicit list of undirected edges (i, j, a_e),
+ * e.g. the grid with diagonals; returns 0 or -1. */
+static int build_graph_edges(int64_t n, const double* w, int64_t nedges,
+                             const int64_t* ei, const int64_t* ej, const double* ae,
+                             graph_t* g, int64_t* wplus)
+{
+    memset(g, 0, sizeof(*g));
+    int64_t npairs = 2 * n + nedges;
+    g->nn = n + 2;
+    g->na = 2 * npairs;
+    int64_t* tail = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    int64_t* hd = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    int64_t* cp = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    g->first = (int64_t*)calloc((size_t)(g->nn + 1), sizeof(int64_t));
+    g->head = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    g->cap = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    g->rev = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->na);
+    if (!tail || !hd || !cp || !g->first || !g->head || !g->cap || !g->rev) {
+        free(tail); free(hd); free(cp);
+        return -1;
+    }
+    int64_t s = n, t = n + 1, na = 0, wp = 0;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!is_integral(w[i])) bad = 1;
+        int64_t wi = (int64_t)w[i];
+        if (wi > 0) wp += wi;
+        tail[na] = s; hd[na] = i; cp[na] = wi > 0 ? wi : 0; ++na;
+        tail[na] = i; hd[na] = s; cp[na] = 0; ++na;
+        tail[na] = i; hd[na] = t; cp[na] = wi < 0 ? -wi : 0; ++na;
+        tail[na] = t; hd[na] = i; cp[na] = 0; ++na;
+    }
+    for (int64_t e = 0; e < nedges; ++e) {
+        if (!is_integral(ae[e]) || ae[e] < 0 || ei[e] < 0 || ei[e] >= n || ej[e] < 0 || ej[e] >= n) bad = 1;
+        int64_t c = (int64_t)ae[e];
+        tail[na] = ei[e]; hd[na] = ej[e]; cp[na] = c; ++na;
+        tail[na] = ej[e]; hd[na] = ei[e]; cp[na] = c; ++na;
+    }
+    if (bad) {
+        free(tail); free(hd); free(cp);
+        return -1;
+    }
+    for (int64_t e = 0; e < na; ++e) g->first[tail[e] + 1]++;
+    for (int64_t u = 0; u < g->nn; ++u) g->first[u + 1] += g->first[u];
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->nn);
+    int64_t* where = (int64_t*)malloc(sizeof(int64_t) * (size_t)na);
+    memcpy(pos, g->first, sizeof(int64_t) * (size_t)g->nn);
+    for (int64_t e = 0; e < na; ++e) {
+        int64_t p = pos[tail[e]]++;
+        where[e] = p;
+        g->head[p] = hd[e];
+        g->cap[p] = cp[e];
+    }
+    for (int64_t e = 0; e < na; ++e) g->rev[where[e]] = where[e ^ 1];
+    free(pos); free(where); free(tail); free(hd); free(cp);
+    *wplus = wp;
+    return 0;
+}
+
+static void finish_maxflow(graph_t* g, int method, int64_t* flow, int64_t* emin,
+                           uint8_t* s_max, int64_t wplus);
+
+int oracle_maxflow_edges(int method, int64_t n, const double* w, int64_t nedges,
+                         const int64_t* ei, const int64_t* ej, const double* ae,
+                         int64_t* flow, int64_t* emin, uint8_t* s_max)
+{
+    if (n < 1 || nedges < 0 || (method != 0 && method != 1)) return -1;
+    graph_t g;
+    int64_t wplus = 0;
+    if (build_graph_edges(n, w, nedges, ei, ej, ae, &g, &wplus) != 0) {
+        free_graph(&g);
+        return -1;
+    }
+    finish_maxflow(&g, method, flow, emin, s_max, wplus);
+    free_graph(&g);
+    return 0;
+}
+
+static void finish_maxflow(graph_t* g, int method, int64_t* flow, int64_t* emin,
+                           uint8_t* s_max, int64_t wplus)
+{
+    int64_t n = g->nn - 2, s = n, t = n + 1;
+    int64_t f = method == 0 ? edmonds_karp(g, s, t) : push_relabel(g, s, t);
+    if (s_max) {
+        int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->nn);
+        int64_t* q = (int64_t*)malloc(sizeof(int64_t) * (size_t)g->nn);
+        distances_to_sink(g, t, d, q);
+        for (int64_t i = 0; i < n; ++i) s_max[i] = (uint8_t)(d[i] >= g->nn);
+        free(d); free(q);
+    }
+    *flow = f;
+    *emin = f - wplus;
+}
+
 int oracle_maxflow(int method, int ndim, const int64_t* dims, const double* w,
                    const double* const* a, int64_t* flow, int64_t* emin,
                    uint8_t* s_max)

@@ -89,6 +89,13 @@ int oracle_bruteforce(int ndim, const int64_t* dims, const double* w,
  * relabelling.  Writes the flow value, E* = flow - sum_i max(w_i,0), and the
  * maximal minimising labelling (vertices that cannot reach t in the residual
  * graph).  Returns 0, or -1 on bad (non-integral or negative) input. */
+/* The same for an explicit list of undirected edges (ei[e], ej[e]) with
+ * weights ae[e] (integers >= 0) over n vertices, e.g. a grid with its
+ * diagonals (8-connected).  Returns 0, -1 on bad input. */
+int oracle_maxflow_edges(int method, int64_t n, const double* w, int64_t nedges,
+                         const int64_t* ei, const int64_t* ej, const double* ae,
+                         int64_t* flow, int64_t* emin, uint8_t* s_max);
+
 int oracle_maxflow(int method, int ndim, const int64_t* dims, const double* w,
                    const double* const* a, int64_t* flow, int64_t* emin,
                    uint8_t* s_max);

@@ -10,7 +10,8 @@ Workloads (stand-ins for the vision grids of the paper's experiments, whose
 max-flow benchmark datasets are not available here):
 
 - ``uniform_grid``: w ~ U{-50..50}, a ~ U{1..20} per edge, int32 (the small
-  exact-check grid and each grid of the batched workload).
+  exact-check grid and each grid of the batched workload); ``uniform_grid8``
+  the same on a 2D 8-connected grid (four weight arrays).
 - ``segmentation_problem``: a blob image (sum of Gaussian blobs plus N(0, 0.1^2)
   noise, clipped to [0, 1]) turned into a two-class segmentation energy:
   unary = log-likelihood ratio of N(0.8, 0.15^2) vs N(0.2, 0.15^2), edge weight
@@ -44,6 +45,20 @@ def uniform_grid(dims, seed: int, w_range=(-50, 50), a_range=(1, 20)):
     w = g.integers(w_range[0], w_range[1], size=dims, endpoint=True, dtype=np.int64).astype(np.int32)
     a = [g.integers(a_range[0], a_range[1], size=compact_shape(dims, k), endpoint=True,
                     dtype=np.int64).astype(np.int32) for k in range(len(dims))]
+    return w, a
+
+
+def uniform_grid8(dims, seed: int, w_range=(-50, 50), a_range=(1, 20)):
+    """A 2D 8-connected grid: w int32 uniform in w_range and four int32 weight
+    arrays uniform in a_range: vertical (H-1, W), horizontal (H, W-1),
+    diagonal (r, c)-(r+1, c+1) and anti-diagonal (r, c+1)-(r+1, c), both
+    (H-1, W-1)."""
+    g = _rng(seed)
+    H, W = (int(d) for d in dims)
+    w = g.integers(w_range[0], w_range[1], size=(H, W), endpoint=True, dtype=np.int64).astype(np.int32)
+    shapes = [(H - 1, W), (H, W - 1), (max(H - 1, 0), max(W - 1, 0)), (max(H - 1, 0), max(W - 1, 0))]
+    a = [g.integers(a_range[0], a_range[1], size=sh, endpoint=True, dtype=np.int64).astype(np.int32)
+         for sh in shapes]
     return w, a
 
 
