@@ -106,7 +106,18 @@ typedef struct {
                             signs of iterates on regions where x* is exactly 0.
                             Default 8 (at most 8); 0 thresholds at `threshold`
                             only */
-    int reserved[7];     /* must be zero */
+    int connectivity;    /* 0 (default) or 4 / 6: edges along the axes (2D
+                            4-connected, 3D 6-connected); 8: a 2D grid that
+                            also has diagonal and anti-diagonal edges, split
+                            (Sec. 3.1, Fig. 2 middle) into columns, rows and
+                            two blocks of zig-zag paths between rows (2p, 2p+1)
+                            and (2p+1, 2p+2); weights axis 2 = diagonal edges
+                            (r, c)-(r+1, c+1), axis 3 = anti-diagonal edges
+                            (r, c+1)-(r+1, c), both (H-1) x (W-1) row-major.
+                            8 needs ndim 2, algo TVCUT_AAR or TVCUT_AP and the
+                            scan schedule (mapping -1, 0 or 5..9); states then
+                            have 4*n values */
+    int reserved[6];     /* must be zero */
 } tvcut_params;
 
 typedef struct {

@@ -157,6 +157,17 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckArgs<T> A)
                 const T x2 = A.x[g + Hm * W];
                 add_edge(xd, x2, qg, level_of(x2), A.a[0][g]);
             }
+            // 8-connected 2D grid: edges to (h+1, c+1) and (h+1, c-1)
+            if (A.adiag && h + 1 < Hm) {
+                if (c + 1 < W) {
+                    const T x2 = A.x[g + W + 1];
+                    add_edge(xd, x2, qg, level_of(x2), A.adiag[h * (W - 1) + c]);
+                }
+                if (c >= 1) {
+                    const T x2 = A.x[g + W - 1];
+                    add_edge(xd, x2, qg, level_of(x2), A.aanti[h * (W - 1) + c - 1]);
+                }
+            }
         }
     }
     acc.xabs = (double)xabs;

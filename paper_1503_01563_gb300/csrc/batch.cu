@@ -497,7 +497,8 @@ extern "C" tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvc
     tvcut_default_params(&prm);
     if (p) prm = *p;
     if ((prm.algo != TVCUT_AAR && prm.algo != TVCUT_AP && prm.algo != TVCUT_FISTA) || (prm.iterate_dtype != TVCUT_F32 && prm.iterate_dtype != TVCUT_F64) ||
-        prm.level_sets < 0 || 2 * prm.level_sets + 1 > kMaxLevels || prm.threshold != prm.threshold)
+        prm.level_sets < 0 || 2 * prm.level_sets + 1 > kMaxLevels || prm.threshold != prm.threshold ||
+        (prm.connectivity != 0 && prm.connectivity != 4))
         return bfail(nullptr, TVCUT_ERR_INVALID, "tvcut_batch_create: bad params");
     tvcut_batch_t b = new tvcut_batch_ctx();
     b->G = G;

@@ -601,7 +601,185 @@ cudaError_t launch_fista_prepare(const FistaArgs<T>& A, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---- 8-connected 2D grids ------------------------------------------------------
+
+template <typename T>
+__global__ void zz_weights_kernel(const T* __restrict__ ad, const T* __restrict__ aa, T* __restrict__ wz, int H,
+                                  int W, int block)
+{
+    const int64_t total = (int64_t)(W - 1) * H;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / H), q = (int)(i - (int64_t)c * H);
+        const int r0 = zz_row(q, c, H, block), r1 = zz_row(q, c + 1, H, block);
+        T v = T(0);
+        if (r1 == r0 + 1) v = ad[(int64_t)r0 * (W - 1) + c];          // diagonal (r0, c)-(r0+1, c+1)
+        else if (r1 == r0 - 1) v = aa[(int64_t)r1 * (W - 1) + c];     // anti-diagonal (r1, c+1)-(r1+1, c)
+        wz[i] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_zz_weights(const T* ad, const T* aa, T* wz, int H, int W, int block, cudaStream_t s)
+{
+    const int64_t total = (int64_t)(W - 1) * H;
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    zz_weights_kernel<T><<<blocks, 256, 0, s>>>(ad, aa, wz, H, W, block);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void zz_relayout_kernel(const T* __restrict__ in, T* __restrict__ out, int H, int W, int block,
+                                   int to_paths)
+{
+    const int64_t total = (int64_t)H * W;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        if (to_paths) {          // out[c * H + q] = vertex (zz_row(q, c), c)
+            const int c = (int)(i / H), q = (int)(i - (int64_t)c * H);
+            out[i] = in[(int64_t)zz_row(q, c, H, block) * W + c];
+        } else {                 // out[r * W + c] = position c * H + zz_row(r, c)
+            const int r = (int)(i / W), c = (int)(i - (int64_t)r * W);
+            out[i] = in[(int64_t)c * H + zz_row(r, c, H, block)];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_zz_relayout(const T* in, T* out, int H, int W, int block, bool to_paths, cudaStream_t s)
+{
+    const int64_t total = (int64_t)H * W;
+    if (total <= 0) return cudaSuccess;
+    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    zz_relayout_kernel<T><<<blocks, 256, 0, s>>>(in, out, H, W, block, to_paths ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// AAR / AP update (or the primal only) of an 8-connected 2D grid, four
+// blocks.  A CTA owns 32 x 32 vertices.  The row block (transposed) is
+// staged like in update_kernel; the two path blocks are staged over the path
+// positions q in [r0 - 1, r0 + 33) of the tile's columns, which hold every
+// position of the tile's vertices (a path leaves its row by at most one), and
+// only the positions whose vertex lies in the tile are written back.
+constexpr int kZzWin = kTile + 2;
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kUpdThreads) update8_kernel(Update8Args<T> A)
+{
+    extern __shared__ __align__(16) unsigned char u8sm[];
+    typedef T Tile1[kTile + 1];
+    typedef T TileZ[kZzWin + 1];
+    Tile1* sz1 = (Tile1*)u8sm;                       // [col][row]
+    Tile1* sx1 = sz1 + kTile;
+    TileZ* sz2 = (TileZ*)(sx1 + kTile);              // [col][q - (r0 - 1)]
+    TileZ* sx2 = sz2 + kTile;
+    TileZ* sz3 = sx2 + kTile;
+    TileZ* sx3 = sz3 + kTile;
+    const int64_t R = A.rows, W = A.cols;
+    const int H = (int)R;
+    const int64_t tiles_c = (W + kTile - 1) / kTile;
+    const int64_t r0 = (blockIdx.x / tiles_c) * kTile;
+    const int64_t c0 = (blockIdx.x % tiles_c) * kTile;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+#pragma unroll
+    for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+        const int64_t c = c0 + cc, r = r0 + tx;
+        if (c < W && r < R) {
+            sz1[cc][tx] = A.s[1][c * R + r];
+            sx1[cc][tx] = A.x[1][c * R + r];
+        }
+    }
+    for (int idx = threadIdx.x; idx < kTile * kZzWin; idx += kUpdThreads) {
+        const int cc = idx / kZzWin, qq = idx - cc * kZzWin;
+        const int64_t c = c0 + cc, q = r0 - 1 + qq;
+        if (c < W && q >= 0 && q < R) {
+            sz2[cc][qq] = A.s[2][c * R + q];
+            sx2[cc][qq] = A.x[2][c * R + q];
+            sz3[cc][qq] = A.s[3][c * R + q];
+            sx3[cc][qq] = A.x[3][c * R + q];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTile; rr += kUpdThreads / kTile) {
+        const int64_t r = r0 + rr, c = c0 + tx;
+        if (r >= R || c >= W) continue;
+        const int64_t g = r * W + c;
+        const int q2 = zz_row((int)r, (int)c, H, 2) - (int)(r0 - 1);
+        const int q3 = zz_row((int)r, (int)c, H, 3) - (int)(r0 - 1);
+        const T wg = A.w[g];
+        const T sv[4] = {A.s[0][g], sz1[tx][rr], sz2[tx][q2], sz3[tx][q3]};
+        const T xv[4] = {A.x[0][g], sx1[tx][rr], sx2[tx][q2], sx3[tx][q3]};
+        T yk[4];
+        T ysum = T(0), ssum = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yk[k] = sv[k] - xv[k];
+            ysum += yk[k];
+            ssum += sv[k];
+        }
+        if (A.check) A.xout[g] = wg - ysum;
+        if constexpr (MODE != UPD_EVAL) {
+            T cc;
+            if constexpr (MODE == UPD_AAR) cc = (wg - T(2) * ysum + ssum) / T(4);
+            else cc = (wg - ysum) / T(4);
+            A.s[0][g] = yk[0] + cc;
+            sz1[tx][rr] = yk[1] + cc;
+            sz2[tx][q2] = yk[2] + cc;
+            sz3[tx][q3] = yk[3] + cc;
+        }
+    }
+    if constexpr (MODE != UPD_EVAL) {
+        __syncthreads();
+#pragma unroll
+        for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+            const int64_t c = c0 + cc, r = r0 + tx;
+            if (c < W && r < R) A.s[1][c * R + r] = sz1[cc][tx];
+        }
+        for (int idx = threadIdx.x; idx < kTile * kZzWin; idx += kUpdThreads) {
+            const int cc = idx / kZzWin, qq = idx - cc * kZzWin;
+            const int64_t c = c0 + cc, q = r0 - 1 + qq;
+            if (c >= W || q < 0 || q >= R) continue;
+            const int64_t v2 = zz_row((int)q, (int)c, H, 2), v3 = zz_row((int)q, (int)c, H, 3);
+            if (v2 >= r0 && v2 < r0 + kTile) A.s[2][c * R + q] = sz2[cc][qq];
+            if (v3 >= r0 && v3 < r0 + kTile) A.s[3][c * R + q] = sz3[cc][qq];
+        }
+    }
+}
+
+template <typename T>
+static size_t update8_smem()
+{
+    return sizeof(T) * (2 * (size_t)kTile * (kTile + 1) + 4 * (size_t)kTile * (kZzWin + 1));
+}
+
+template <typename T>
+cudaError_t launch_update8(int mode, const Update8Args<T>& A, cudaStream_t s)
+{
+    const int64_t tiles = ((A.rows + kTile - 1) / kTile) * ((A.cols + kTile - 1) / kTile);
+    if (tiles == 0) return cudaSuccess;
+    const size_t smem = update8_smem<T>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(update8_kernel<T, UPD_AAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(update8_kernel<T, UPD_AP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(update8_kernel<T, UPD_EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    if (mode == UPD_AAR) update8_kernel<T, UPD_AAR><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    else if (mode == UPD_AP) update8_kernel<T, UPD_AP><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    else update8_kernel<T, UPD_EVAL><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
 #define TVCUT_SCAN_INST(T)                                                                  \
+    template cudaError_t launch_update8<T>(int, const Update8Args<T>&, cudaStream_t);       \
+    template cudaError_t launch_zz_weights<T>(const T*, const T*, T*, int, int, int, cudaStream_t); \
+    template cudaError_t launch_zz_relayout<T>(const T*, T*, int, int, int, bool, cudaStream_t); \
     template cudaError_t launch_fista_prepare<T>(const FistaArgs<T>&, cudaStream_t);        \
     template cudaError_t launch_bcd_prepare<T>(const UpdateArgs<T>&, int, cudaStream_t);    \
     template cudaError_t launch_scan<T>(ScanArgs<T>, cudaStream_t);                         \

@@ -24,6 +24,8 @@ using namespace tvcut;
 
 struct tvcut_ctx {
     int ndim = 0;
+    int nblk = 0;                  // blocks: ndim, or 4 for an 8-connected 2D grid
+    bool conn8 = false;
     int64_t dims[3] = {1, 1, 1};
     int64_t n = 0;
     tvcut_params p;
@@ -31,8 +33,10 @@ struct tvcut_ctx {
     int esize = 4;                 // bytes of the iterate type
     void* state = nullptr;         // ndim * n
     void* w = nullptr;             // n
-    void* a[3] = {nullptr, nullptr, nullptr};
-    int64_t a_len[3] = {0, 0, 0};
+    void* a[4] = {nullptr, nullptr, nullptr, nullptr};   // per block, in the block's layout
+    int64_t a_len[4] = {0, 0, 0, 0};                      // input length per weight axis
+    void* adiag = nullptr;         // 8-connected: diagonal / anti-diagonal weights, (H-1) x (W-1) row-major
+    void* aanti = nullptr;
     void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
     void* xk = nullptr;            // ndim * n: per-block prox outputs of the scan schedule
     void* yprev = nullptr;         // FISTA: ndim * n, the previous iterate (swaps with state)
@@ -45,8 +49,8 @@ struct tvcut_ctx {
     double wmax = 0.0;             // max |w|: scale of the level-set ladder
     DevStatus* dstatus = nullptr;
     DevStatus* hstatus = nullptr;  // pinned
-    bool have_w = false, have_a[3] = {false, false, false};
-    bool int_w = false, int_a[3] = {false, false, false};
+    bool have_w = false, have_a[4] = {false, false, false, false};
+    bool int_w = false, int_a[4] = {false, false, false, false};
     bool x_valid = false, labels_valid = false;
     int64_t iters = 0;
     tvcut_stats last;
@@ -110,7 +114,9 @@ extern "C" void tvcut_destroy(tvcut_t h)
     if (!h) return;
     cudaFree(h->state);
     cudaFree(h->w);
-    for (int k = 0; k < 3; ++k) cudaFree(h->a[k]);
+    for (int k = 0; k < 4; ++k) cudaFree(h->a[k]);
+    cudaFree(h->adiag);
+    cudaFree(h->aanti);
     cudaFree(h->scratch);
     cudaFree(h->xk);
     cudaFree(h->yprev);
@@ -140,7 +146,15 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
-    for (int i = 0; i < 7; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
+    for (int i = 0; i < 6; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
+    if (p->connectivity != 0 && p->connectivity != 4 && p->connectivity != 6 && p->connectivity != 8) {
+        why = "params.connectivity must be 0, 4, 6 or 8";
+        return false;
+    }
+    if (p->connectivity == 8 && ((p->algo != TVCUT_AAR && p->algo != TVCUT_AP) || (p->mapping >= 1 && p->mapping <= 4))) {
+        why = "connectivity 8 runs TVCUT_AAR or TVCUT_AP on the scan schedule (mapping -1, 0 or 5..9)";
+        return false;
+    }
     return true;
 }
 
@@ -164,8 +178,13 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     std::string why;
     if (!valid_params(&prm, why)) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: " + why);
 
+    if ((prm.connectivity == 8 && ndim != 2) || (prm.connectivity == 4 && ndim != 2) ||
+        (prm.connectivity == 6 && ndim != 3))
+        return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_create: connectivity 4 and 8 need ndim 2, 6 needs ndim 3");
     tvcut_t h = new tvcut_ctx();
     h->ndim = ndim;
+    h->conn8 = prm.connectivity == 8;
+    h->nblk = h->conn8 ? 4 : ndim;
     for (int k = 0; k < ndim; ++k) h->dims[k] = dims[k];
     h->n = n;
     h->p = prm;
@@ -175,15 +194,23 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
     memset(&h->last, 0, sizeof(h->last));
     const size_t es = (size_t)h->esize;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&h->state, es * (size_t)(ndim * n));
+    const int nb = h->nblk;
+    if (e == cudaSuccess) e = cudaMalloc(&h->state, es * (size_t)(nb * n));
     if (e == cudaSuccess) e = cudaMalloc(&h->w, es * (size_t)n);
     for (int k = 0; k < ndim && e == cudaSuccess; ++k) {
         h->a_len[k] = n / dims[k] * (dims[k] - 1);
         e = cudaMalloc(&h->a[k], es * (size_t)(h->a_len[k] > 0 ? h->a_len[k] : 1));
     }
+    if (h->conn8) {                // path weights of blocks 2, 3 ((W-1) x H) and the diagonal inputs
+        const int64_t nd = (dims[0] - 1) * (dims[1] - 1), nz = (dims[1] - 1) * dims[0];
+        h->a_len[2] = h->a_len[3] = nd;
+        for (int k = 2; k < 4 && e == cudaSuccess; ++k) e = cudaMalloc(&h->a[k], es * (size_t)(nz > 0 ? nz : 1));
+        if (e == cudaSuccess) e = cudaMalloc(&h->adiag, es * (size_t)(nd > 0 ? nd : 1));
+        if (e == cudaSuccess) e = cudaMalloc(&h->aanti, es * (size_t)(nd > 0 ? nd : 1));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
-    if (e == cudaSuccess) e = cudaMalloc(&h->xk, es * (size_t)(ndim * n));
-    if (e == cudaSuccess && prm.algo == TVCUT_FISTA) e = cudaMalloc(&h->yprev, es * (size_t)(ndim * n));
+    if (e == cudaSuccess) e = cudaMalloc(&h->xk, es * (size_t)(nb * n));
+    if (e == cudaSuccess && prm.algo == TVCUT_FISTA) e = cudaMalloc(&h->yprev, es * (size_t)(nb * n));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->labels, (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(CheckPartial) * kCheckBlocks);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->level_partials, sizeof(LevelPartial) * kCheckBlocks);
@@ -225,6 +252,62 @@ static cudaError_t relayout(tvcut_t h, T* arr, int64_t rows, int64_t cols, bool 
                             : launch_transpose<T>(arr, tmp, cols, rows, h->stream);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(arr, tmp, sizeof(T) * (size_t)(rows * cols), cudaMemcpyDeviceToDevice, h->stream);
+}
+
+// Layout of block k's state and weights in the scan schedule: 0 natural, 1
+// transposed (the last axis' block), 2 / 3 the zig-zag path layouts of an
+// 8-connected grid.
+static int block_layout(tvcut_t h, int k)
+{
+    if (h->conn8 && k >= 2) return k;
+    return (h->tlast && k == h->ndim - 1) ? 1 : 0;
+}
+
+// Scan geometry of block k (chains of the axis, or the H zig-zag paths of length W).
+template <typename T>
+static ScanAxis<T> block_axis(tvcut_t h, int k, const T* v, T* x)
+{
+    ScanAxis<T> X;
+    memset(&X, 0, sizeof(X));
+    if (block_layout(h, k) >= 2) {
+        X.nchains = h->dims[0];
+        X.inner = 1;
+        X.m = (int)h->dims[1];
+        X.transposed = 1;
+    } else {
+        ChainGeom g = chain_geom(h->ndim, h->dims, k);
+        X.nchains = g.nchains;
+        X.inner = g.inner;
+        X.m = g.m;
+        X.transposed = block_layout(h, k) == 1 ? 1 : 0;
+    }
+    X.v = v;
+    X.a = (const T*)h->a[k];
+    X.x = x;
+    return X;
+}
+
+// Block k of a state from grid layout to its own, in place (through the xk area).
+template <typename T>
+static cudaError_t to_internal(tvcut_t h, int k, T* arr)
+{
+    const int L = block_layout(h, k);
+    if (L == 0) return cudaSuccess;
+    if (L == 1) return relayout<T>(h, arr, rows_of(h), cols_of(h), true);
+    T* tmp = XK_of<T>(h, 0);
+    cudaError_t e = launch_zz_relayout<T>(arr, tmp, (int)h->dims[0], (int)h->dims[1], L, true, h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(arr, tmp, sizeof(T) * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream);
+}
+
+// Block k of a state from its own layout to grid layout, out of place.
+template <typename T>
+static cudaError_t to_natural(tvcut_t h, int k, const T* arr, T* out)
+{
+    const int L = block_layout(h, k);
+    if (L == 0) return cudaMemcpyAsync(out, arr, sizeof(T) * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream);
+    if (L == 1) return launch_transpose<T>(arr, out, cols_of(h), rows_of(h), h->stream);
+    return launch_zz_relayout<T>(arr, out, (int)h->dims[0], (int)h->dims[1], L, false, h->stream);
 }
 
 // ---- tracing ----------------------------------------------------------------
@@ -315,7 +398,7 @@ static cudaError_t restart_momentum(tvcut_t h)
 {
     h->fista_tprev = h->fista_t = 1.0;
     if (h->p.algo != TVCUT_FISTA) return cudaSuccess;
-    return cudaMemcpyAsync(h->yprev, h->state, (size_t)h->esize * (size_t)(h->ndim * h->n),
+    return cudaMemcpyAsync(h->yprev, h->state, (size_t)h->esize * (size_t)(h->nblk * h->n),
                            cudaMemcpyDeviceToDevice, h->stream);
 }
 
@@ -323,13 +406,12 @@ template <typename T>
 static tvcut_status cold_start(tvcut_t h)
 {
     if (h->p.algo == TVCUT_AP) {
-        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_cold_ap<T>((const T*)h->w, (T*)h->state, h->ndim, h->n, h->stream); }),
+        CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_cold_ap<T>((const T*)h->w, (T*)h->state, h->nblk, h->n, h->stream); }),
            "cold start");
-        if (h->tlast)
-            CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true); }),
-               "cold start");
+        for (int k = 0; k < h->nblk; ++k)
+            CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return to_internal<T>(h, k, S_of<T>(h, k)); }), "cold start");
     } else {
-        CK(h, cudaMemsetAsync(h->state, 0, (size_t)h->esize * (size_t)(h->ndim * h->n), h->stream), "cold start");
+        CK(h, cudaMemsetAsync(h->state, 0, (size_t)h->esize * (size_t)(h->nblk * h->n), h->stream), "cold start");
     }
     CK(h, restart_momentum(h), "cold start");
     h->iters = 0;
@@ -340,7 +422,7 @@ static tvcut_status cold_start(tvcut_t h)
 static bool inputs_ready(tvcut_t h)
 {
     if (!h->have_w) return false;
-    for (int k = 0; k < h->ndim; ++k) if (!h->have_a[k]) return false;
+    for (int k = 0; k < h->nblk; ++k) if (!h->have_a[k]) return false;
     return true;
 }
 
@@ -494,20 +576,25 @@ static cudaError_t run_iteration(tvcut_t h, int mode, int check)
     const int r = h->ndim;
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
-    S.naxes = r;
+    S.naxes = h->nblk;
     S.force = scan_force(h->p.mapping);
-    for (int k = 0; k < r; ++k) {
-        ChainGeom g = chain_geom(h->ndim, h->dims, k);
-        S.ax[k].nchains = g.nchains;
-        S.ax[k].inner = g.inner;
-        S.ax[k].m = g.m;
-        S.ax[k].transposed = k == r - 1 ? 1 : 0;
-        S.ax[k].v = S_of<T>(h, k);
-        S.ax[k].a = (const T*)h->a[k];
-        S.ax[k].x = XK_of<T>(h, k);
-    }
+    for (int k = 0; k < h->nblk; ++k) S.ax[k] = block_axis<T>(h, k, S_of<T>(h, k), XK_of<T>(h, k));
     cudaError_t e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
     if (e != cudaSuccess) return e;
+    if (h->conn8) {                // four blocks: rows, columns and the two path blocks
+        Update8Args<T> U8;
+        memset(&U8, 0, sizeof(U8));
+        U8.rows = h->dims[0];
+        U8.cols = h->dims[1];
+        U8.check = check;
+        for (int k = 0; k < 4; ++k) {
+            U8.s[k] = S_of<T>(h, k);
+            U8.x[k] = XK_of<T>(h, k);
+        }
+        U8.w = (const T*)h->w;
+        U8.xout = X_of<T>(h);
+        return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_update8<T>(mode, U8, h->stream); });
+    }
     UpdateArgs<T> U;
     memset(&U, 0, sizeof(U));
     U.rows = rows_of(h);
@@ -539,6 +626,10 @@ static tvcut_status run_check(tvcut_t h)
     C.x = X_of<T>(h);
     C.w = (const T*)h->w;
     C.labels = h->labels;
+    if (h->conn8) {
+        C.adiag = (const T*)h->adiag;
+        C.aanti = (const T*)h->aanti;
+    }
     C.threshold = (T)h->p.threshold;
     C.last_transposed = h->tlast ? 1 : 0;
     C.partials = h->partials;
@@ -563,7 +654,7 @@ static tvcut_status run_check(tvcut_t h)
     for (int q = 0; q < L; ++q) C.levels[q] = (T)lv[order[q]];
     C.level_partials = h->level_partials;
     bool exact_data = h->int_w;
-    for (int k = 0; k < h->ndim; ++k) exact_data = exact_data && h->int_a[k];
+    for (int k = 0; k < h->nblk; ++k) exact_data = exact_data && h->int_a[k];
     CK(h, traced(h, TVCUT_K_CHECK, 3, [&] { return launch_check<T>(C, exact_data, h->dstatus, h->stream); }),
        "check");
     CK(h, cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream), "check");
@@ -573,7 +664,7 @@ static tvcut_status run_check(tvcut_t h)
     tvcut_stats& st = h->last;
     memset(&st, 0, sizeof(st));
     bool exact = h->int_w;
-    for (int k = 0; k < h->ndim; ++k) exact = exact && h->int_a[k];
+    for (int k = 0; k < h->nblk; ++k) exact = exact && h->int_a[k];
     st.iters = h->iters;
     // keep the lowest-energy level set; ties go to the earlier ladder entry
     // (the plain threshold first)
@@ -666,10 +757,20 @@ extern "C" tvcut_status tvcut_set_unary(tvcut_t h, const void* w, int dtype, int
 template <typename T>
 static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dtype, int space)
 {
-    tvcut_status st = ingest<T>(h, a, dtype, space, h->a_len[axis], true, (T*)h->a[axis], "tvcut_set_weights");
+    // 8-connected: axes 2, 3 are the diagonal inputs, kept in grid layout for
+    // the check; the two path blocks' weights are built from both of them
+    const bool diag = h->conn8 && axis >= 2;
+    T* dst = diag ? (T*)(axis == 2 ? h->adiag : h->aanti) : (T*)h->a[axis];
+    tvcut_status st = ingest<T>(h, a, dtype, space, h->a_len[axis], true, dst, "tvcut_set_weights");
     if (st != TVCUT_OK) { h->have_a[axis] = false; return st; }
     if (h->tlast && axis == h->ndim - 1)
         CK(h, relayout<T>(h, (T*)h->a[axis], rows_of(h), cols_of(h) - 1, true), "tvcut_set_weights");
+    if (diag && (h->have_a[5 - axis] || h->a_len[axis] == 0)) {
+        for (int b = 2; b < 4; ++b)
+            CK(h, launch_zz_weights<T>((const T*)h->adiag, (const T*)h->aanti, (T*)h->a[b], (int)h->dims[0],
+                                       (int)h->dims[1], b, h->stream),
+               "tvcut_set_weights");
+    }
     h->have_a[axis] = true;
     h->int_a[axis] = dtype == TVCUT_I32;
     if (h->have_w) return cold_start<T>(h);
@@ -679,7 +780,7 @@ static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dty
 extern "C" tvcut_status tvcut_set_weights(tvcut_t h, int axis, const void* a, int dtype, int space)
 {
     if (!h) return fail(nullptr, TVCUT_ERR_INVALID, "tvcut_set_weights: NULL handle");
-    if (axis < 0 || axis >= h->ndim) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_weights: axis out of range");
+    if (axis < 0 || axis >= h->nblk) return fail(h, TVCUT_ERR_INVALID, "tvcut_set_weights: axis out of range");
     return DISPATCH(h, set_weights_impl, h, axis, a, dtype, space);
 }
 
@@ -764,15 +865,15 @@ extern "C" tvcut_status tvcut_get_primal(tvcut_t h, void* x, int dtype, int spac
 template <typename T>
 static tvcut_status get_state_impl(tvcut_t h, void* s, int space)
 {
-    const int r = h->ndim;
     const cudaMemcpyKind kind = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    const int plain = h->tlast ? r - 1 : r;
-    CK(h, cudaMemcpyAsync(s, h->state, sizeof(T) * (size_t)(plain * h->n), kind, h->stream), "tvcut_get_state");
-    if (h->tlast) {
-        // the last block back to grid layout through the xk area
-        T* tmp = XK_of<T>(h, 0);
-        CK(h, launch_transpose<T>(S_of<T>(h, r - 1), tmp, cols_of(h), rows_of(h), h->stream), "tvcut_get_state");
-        CK(h, cudaMemcpyAsync((T*)s + (int64_t)(r - 1) * h->n, tmp, sizeof(T) * (size_t)h->n, kind, h->stream),
+    for (int k = 0; k < h->nblk; ++k) {
+        const T* src = S_of<T>(h, k);
+        if (block_layout(h, k) != 0) {         // back to grid layout through the xk area
+            T* tmp = XK_of<T>(h, 0);
+            CK(h, to_natural<T>(h, k, src, tmp), "tvcut_get_state");
+            src = tmp;
+        }
+        CK(h, cudaMemcpyAsync((T*)s + (int64_t)k * h->n, src, sizeof(T) * (size_t)h->n, kind, h->stream),
            "tvcut_get_state");
     }
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_state");
@@ -792,32 +893,23 @@ extern "C" tvcut_status tvcut_get_state(tvcut_t h, void* s, int space)
 template <typename T>
 static tvcut_status get_dual_impl(tvcut_t h, void* out, int space)
 {
-    const int r = h->ndim;
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
-    S.naxes = r;
-    for (int k = 0; k < r; ++k) {
-        ChainGeom g = chain_geom(h->ndim, h->dims, k);
-        S.ax[k].nchains = g.nchains;
-        S.ax[k].inner = g.inner;
-        S.ax[k].m = g.m;
-        S.ax[k].transposed = (h->tlast && k == r - 1) ? 1 : 0;
-        S.ax[k].v = S_of<T>(h, k);
-        S.ax[k].a = (const T*)h->a[k];
-        S.ax[k].x = XK_of<T>(h, k);
-    }
+    S.naxes = h->nblk;
+    for (int k = 0; k < h->nblk; ++k) S.ax[k] = block_axis<T>(h, k, S_of<T>(h, k), XK_of<T>(h, k));
     S.shadow = 1;                                         // y_k = s_k - prox(s_k)
     CK(h, traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); }), "tvcut_get_dual");
     const cudaMemcpyKind kind = space == TVCUT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    const int plain = h->tlast ? r - 1 : r;
-    CK(h, cudaMemcpyAsync(out, h->xk, sizeof(T) * (size_t)(plain * h->n), kind, h->stream), "tvcut_get_dual");
-    if (h->tlast) {
-        // the last block back to grid layout, through the P|x scratch (2n values)
-        T* tmp = P_of<T>(h);
-        CK(h, launch_transpose<T>(XK_of<T>(h, r - 1), tmp, cols_of(h), rows_of(h), h->stream), "tvcut_get_dual");
-        CK(h, cudaMemcpyAsync((T*)out + (int64_t)(r - 1) * h->n, tmp, sizeof(T) * (size_t)h->n, kind, h->stream),
+    for (int k = 0; k < h->nblk; ++k) {
+        const T* src = XK_of<T>(h, k);
+        if (block_layout(h, k) != 0) {         // back to grid layout through the P|x scratch (2n values)
+            T* tmp = P_of<T>(h);
+            CK(h, to_natural<T>(h, k, src, tmp), "tvcut_get_dual");
+            src = tmp;
+            h->x_valid = h->labels_valid = false;    // the scratch held the primal
+        }
+        CK(h, cudaMemcpyAsync((T*)out + (int64_t)k * h->n, src, sizeof(T) * (size_t)h->n, kind, h->stream),
            "tvcut_get_dual");
-        h->x_valid = h->labels_valid = false;        // the scratch held the primal
     }
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_get_dual");
     return TVCUT_OK;
@@ -837,11 +929,10 @@ extern "C" tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space)
 template <typename T>
 static tvcut_status set_state_impl(tvcut_t h, const void* s, int space)
 {
-    CK(h, cudaMemcpyAsync(h->state, s, sizeof(T) * (size_t)(h->ndim * h->n),
+    CK(h, cudaMemcpyAsync(h->state, s, sizeof(T) * (size_t)(h->nblk * h->n),
                           space == TVCUT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
        "tvcut_set_state");
-    if (h->tlast)
-        CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_set_state");
+    for (int k = 0; k < h->nblk; ++k) CK(h, to_internal<T>(h, k, S_of<T>(h, k)), "tvcut_set_state");
     CK(h, restart_momentum(h), "tvcut_set_state");
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_set_state");
     h->x_valid = h->labels_valid = false;
@@ -866,10 +957,9 @@ static tvcut_status warmstart_impl(tvcut_t h, const float* xhat, float tau, int 
         d = (const float*)h->scratch;
     }
     // the kernel reads xhat[i] before writing state; state and scratch are disjoint
-    CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_warmstart<T>((const T*)h->w, d, tau, (T*)h->state, h->ndim, h->n, h->stream); }),
+    CK(h, traced(h, TVCUT_K_OTHER, 1, [&] { return launch_warmstart<T>((const T*)h->w, d, tau, (T*)h->state, h->nblk, h->n, h->stream); }),
        "tvcut_warmstart_primal");
-    if (h->tlast)
-        CK(h, relayout<T>(h, S_of<T>(h, h->ndim - 1), rows_of(h), cols_of(h), true), "tvcut_warmstart_primal");
+    for (int k = 0; k < h->nblk; ++k) CK(h, to_internal<T>(h, k, S_of<T>(h, k)), "tvcut_warmstart_primal");
     CK(h, restart_momentum(h), "tvcut_warmstart_primal");
     CK(h, cudaStreamSynchronize(h->stream), "tvcut_warmstart_primal");
     h->x_valid = h->labels_valid = false;

@@ -40,7 +40,7 @@ struct ScanArgs {
     int naxes;
     int force;             // 0 automatic, 1 thread per chain, 2/3/4/5: 32/16/8/4 lanes per chain
     int shadow;            // 1: write v - prox(v) (the projection onto K_k) instead of prox(v)
-    ScanAxis<T> ax[3];
+    ScanAxis<T> ax[4];
 };
 
 enum UpdateMode : int { UPD_AAR = 0, UPD_AP = 1, UPD_EVAL = 2 };
@@ -134,6 +134,8 @@ struct CheckArgs {
     int nlevels;                   // level-set ladder size (0: none)
     T levels[kMaxLevels];
     LevelPartial* level_partials;
+    const T* adiag;                // 8-connected 2D grid: diagonal (r, c)-(r+1, c+1) and
+    const T* aanti;                // anti-diagonal (r, c+1)-(r+1, c) weights, (H-1) x (W-1); else null
 };
 
 // Validation flags raised by the conversion kernels.
@@ -174,6 +176,42 @@ template <typename T>
 cudaError_t launch_transpose(const T* in, T* out, int64_t rows, int64_t cols, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bcd_prepare(const UpdateArgs<T>& args, int skip, cudaStream_t s);
+
+// 8-connected 2D grids (Sec. 3.1, Fig. 2 middle): blocks 2 and 3 are the
+// zig-zag paths between rows (2p, 2p+1) and (2p+1, 2p+2).  Path q starts at
+// (q, 0); in column c it sits at row zz_row(q, c) (its partner row in odd
+// columns when row q is paired in that block).  Element c of path q is
+// stored at c * H + q, like the transposed row block, so every path scan is
+// coalesced.  zz_row is an involution in each column, so it also maps a
+// vertex (r, c) to its position: path zz_row(r, c).
+__host__ __device__ __forceinline__ int zz_row(int q, int c, int H, int block)
+{
+    if (!(c & 1)) return q;
+    if (block == 2) return (q ^ 1) < H ? (q ^ 1) : q;
+    if (q == 0) return 0;
+    const int p = 1 + ((q - 1) ^ 1);
+    return p < H ? p : q;
+}
+
+template <typename T>
+struct Update8Args {
+    int64_t rows;          // H
+    int64_t cols;          // W
+    int check;
+    T* s[4];               // block states: natural, transposed, zig-zag (even), zig-zag (odd)
+    const T* x[4];         // block prox outputs, same layouts
+    const T* w;
+    T* xout;
+};
+template <typename T>
+cudaError_t launch_update8(int mode, const Update8Args<T>& args, cudaStream_t s);
+// path weights of block 2 or 3 ((W-1) x H, element c of path q at c * H + q)
+// from the diagonal and anti-diagonal weights ((H-1) x (W-1), natural)
+template <typename T>
+cudaError_t launch_zz_weights(const T* ad, const T* aa, T* wz, int H, int W, int block, cudaStream_t s);
+// natural (H x W) <-> path layout of block 2 or 3
+template <typename T>
+cudaError_t launch_zz_relayout(const T* in, T* out, int H, int W, int block, bool to_paths, cudaStream_t s);
 
 // FISTA step inputs (scan-schedule layout: the last block transposed).
 template <typename T>

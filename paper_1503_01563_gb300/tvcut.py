@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
         ("gap_tol", ctypes.c_double),
         ("threshold", ctypes.c_double),
         ("level_sets", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("connectivity", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -302,12 +303,15 @@ def tvcut_iterate_noalloc(dims, algo, w, a, state, x=None, iters=1, stream=None)
 
 class Solver:
     """One grid: ``Solver(dims, algo=AAR, dtype=F32)``; ``set_problem(w, a)``;
-    ``iterate(k)``; ``cut()``."""
+    ``iterate(k)``; ``cut()``.  ``connectivity=8``: a 2D grid with diagonal
+    edges; ``a`` then holds four arrays (vertical, horizontal, diagonal,
+    anti-diagonal) and states have four blocks."""
 
     def __init__(self, dims, algo=AAR, dtype=F32, check_every=10, gap_tol=0.0, threshold=0.0,
-                 stream=None, level_sets=None, mapping=-1):
+                 stream=None, level_sets=None, mapping=-1, connectivity=0):
         p = tvcut_default_params()
         p.mapping = mapping
+        p.connectivity = connectivity
         if level_sets is not None:
             p.level_sets = level_sets
         p.algo = algo
@@ -318,6 +322,7 @@ class Solver:
         self.dims = tuple(int(d) for d in dims)
         self.n = int(np.prod(self.dims))
         self.dtype = dtype
+        self.nblk = 4 if connectivity == 8 else len(self.dims)
         self.h = tvcut_create(self.dims, p, stream)
 
     def close(self):
@@ -355,13 +360,13 @@ class Solver:
         return x
 
     def state(self):
-        s = np.empty((len(self.dims),) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
+        s = np.empty((self.nblk,) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
         tvcut_get_state(self.h, s)
         return s
 
     def dual(self):
         """Shadow duals y_k of the current state, shape (ndim,) + dims."""
-        y = np.empty((len(self.dims),) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
+        y = np.empty((self.nblk,) + self.dims, dtype=np.float64 if self.dtype == F64 else np.float32)
         _check(lib().tvcut_get_dual(self.h, ctypes.c_void_p(y.ctypes.data), HOST), self.h)
         return y
 
