@@ -35,6 +35,8 @@ WORKLOADS = {
     "volume256": dict(dims=(256, 256, 256), seed=3, cap=1500),
     # 2D 4-connected 1024^2 blob segmentation, integer-scaled LLR unary and contrast weights
     "seg1024": dict(dims=(1024, 1024), seed=2, cap=3000),
+    # the same image on a 2D 8-connected grid (diagonal contrast weights / sqrt(2)): four blocks
+    "seg1024c8": dict(dims=(1024, 1024), seed=2, cap=3000, conn=8),
     # 512 independent 2D grids, H ~ U{64..1024} x W ~ U{64..768}, w ~ U{-50..50}, a ~ U{1..20}
     "batch512": dict(grids=512, seed=4, cap=3000),
     # learned warm start: U-Net (4 levels, 32 channels) trained on solver-generated 128^2 problems,
@@ -59,6 +61,8 @@ def make_problem(name):
         return probs[g]
     if name == "warm2048":
         return inputs.uniform_grid(wl["dims"], wl["seed"])
+    if wl.get("conn") == 8:
+        return inputs.segmentation_problem8(wl["dims"], wl["seed"])
     if len(wl["dims"]) == 3:
         return inputs.volume_problem(wl["dims"], wl["seed"])
     return inputs.segmentation_problem(wl["dims"], wl["seed"])
@@ -171,17 +175,20 @@ def cpu_leg(name, w, a, budget_s=12.0, algo="aar"):
     min-cut value E*."""
     import oracle
     oracle.build()
+    orc = oracle
+    if len(a) == 4:                    # 8-connected 2D grid
+        from oracle import conn8 as orc
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    e_star = oracle.maxflow(w, a, 1)[1]
+    e_star = orc.maxflow(w, a, 1)[1]
     t_mf = time.perf_counter() - t0
     n = int(np.prod(w.shape))
     code = ALGOS[algo]
-    s = oracle.cold_state(code, w)
+    s = orc.cold_state(code, w)
     iters, t_it = 0, 0.0
     while t_it < budget_s and iters < 200:
         t0 = time.perf_counter()
-        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
+        s, _ = orc.iterate(code, w, a, s, 1, nthreads=cores)
         t_it += time.perf_counter() - t0
         iters += 1
     value = n * iters / t_it / 1e6
@@ -202,12 +209,15 @@ def run_reference(args):
     n = int(np.prod(w.shape))
     cores = os.cpu_count() or 1
     code = ALGOS[args.algo]
-    s = oracle.cold_state(code, w)
+    orc = oracle
+    if len(a) == 4:                    # 8-connected 2D grid
+        from oracle import conn8 as orc
+    s = orc.cold_state(code, w)
     for _ in range(args.warmup):
-        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
+        s, _ = orc.iterate(code, w, a, s, 1, nthreads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, _ = oracle.iterate(code, w, a, s, 1, nthreads=cores)
+        s, _ = orc.iterate(code, w, a, s, 1, nthreads=cores)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt / 1e6
     out = {"impl": "reference", "metric": "Mvertex-iter/s", "value": value, "unit": "Mvertex-iter/s",
@@ -643,7 +653,8 @@ def run_ours(args):
     w, a = make_problem(args.workload)
     dims = tuple(w.shape)
     n = int(np.prod(dims))
-    ndim = len(dims)
+    conn = WORKLOADS[args.workload].get("conn", 0)
+    ndim = 4 if conn == 8 else len(dims)          # blocks per iteration
     algo = ALGOS[args.algo]
 
     # CPU leg (rank 0): oracle E* and the oracle's own throughput
@@ -659,7 +670,8 @@ def run_ours(args):
     kstar = None
     cap = WORKLOADS[args.workload]["cap"]
     if rank == 0:
-        probe = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+        probe = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream,
+                             connectivity=conn)
         probe.set_problem(wd, ad)
         for k in range(1, cap + 1):
             _, st = probe.iterate(1)
@@ -673,7 +685,8 @@ def run_ours(args):
         dist.broadcast(t, 0)
         iters = int(t.item())
 
-    solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream,
+                          connectivity=conn)
     solver.set_problem(wd, ad)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -735,7 +748,8 @@ def run_ours(args):
                 "iteration_GBps": float(moved / max((kms[0] + kms[1]) / 1e3, 1e-12) / 1e9)}
 
     # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
-    e2e_solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+    e2e_solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream,
+                              connectivity=conn)
     labels = np.empty(dims, dtype=np.uint8)
     w_pin = torch.from_numpy(w).pin_memory()
     a_pin = [torch.from_numpy(x).pin_memory() for x in a]
@@ -761,6 +775,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "dims": list(dims), "algo": args.algo.upper(), "iterate": "f32",
+                       "connectivity": conn if conn else 2 * len(dims), "blocks": ndim,
                        "iters_per_step": iters, "step": "cold start + iterations to the oracle-equal cut + cut",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB buffer written between steps"},

@@ -114,6 +114,19 @@ def segmentation_problem(dims, seed: int, integer: bool = True, scale: float = 1
     return w.astype(np.float32), [x.astype(np.float32) for x in a]
 
 
+def segmentation_problem8(dims, seed: int, scale: float = 100.0, contrast: float = 10.0, beta: float = 0.05):
+    """The blob-image segmentation energy on a 2D 8-connected grid: weights
+    [vertical, horizontal, diagonal (r, c)-(r+1, c+1), anti-diagonal
+    (r, c+1)-(r+1, c)], the contrast formula on each neighbour pair, the two
+    diagonal directions scaled by 1/sqrt(2); integer-scaled like to_integer."""
+    img = blob_image(dims, seed)
+    w, a = segmentation_terms(img, contrast=contrast, beta=beta)
+    cw = lambda d: contrast * np.exp(-(d * d) / (2.0 * beta * beta))
+    ad = cw(img[1:, 1:] - img[:-1, :-1]) / np.sqrt(2.0)
+    aa = cw(img[1:, :-1] - img[:-1, 1:]) / np.sqrt(2.0)
+    return to_integer(w, a + [ad, aa], scale)
+
+
 def volume_problem(dims, seed: int, a_range=(1, 30), scale: float = 100.0):
     """3D blob-volume unary (integer-scaled LLR) with int32 edge weights
     uniform in a_range."""
