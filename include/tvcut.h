@@ -114,9 +114,8 @@ typedef struct {
                             and (2p+1, 2p+2); weights axis 2 = diagonal edges
                             (r, c)-(r+1, c+1), axis 3 = anti-diagonal edges
                             (r, c+1)-(r+1, c), both (H-1) x (W-1) row-major.
-                            8 needs ndim 2, algo TVCUT_AAR or TVCUT_AP and the
-                            scan schedule (mapping -1, 0 or 5..9); states then
-                            have 4*n values */
+                            8 needs ndim 2 and the scan schedule (mapping -1, 0
+                            or 5..9); states then have 4*n values */
     int reserved[6];     /* must be zero */
 } tvcut_params;
 

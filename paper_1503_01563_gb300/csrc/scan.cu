@@ -776,7 +776,140 @@ cudaError_t launch_update8(int mode, const Update8Args<T>& A, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The dual-iterate passes of an 8-connected grid (BCD, FISTA, primal), staged
+// like update8_kernel: the row block over the tile's rows, the two path blocks
+// over the windows [r0 - 1, r0 + 33) of path positions; outputs in the path
+// layouts go back only at positions whose vertex lies in the tile.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kUpdThreads) prep8_kernel(Prep8Args<T> A)
+{
+    extern __shared__ __align__(16) unsigned char p8sm[];
+    typedef T Tile1[kTile + 1];
+    typedef T TileZ[kZzWin + 1];
+    Tile1* sy1 = (Tile1*)p8sm;
+    Tile1* sp1 = sy1 + kTile;
+    TileZ* sy2 = (TileZ*)(sp1 + kTile);
+    TileZ* sp2 = sy2 + kTile;
+    TileZ* sy3 = sp2 + kTile;
+    TileZ* sp3 = sy3 + kTile;
+    const int64_t R = A.rows, W = A.cols;
+    const int H = (int)R;
+    const int64_t tiles_c = (W + kTile - 1) / kTile;
+    const int64_t r0 = (blockIdx.x / tiles_c) * kTile;
+    const int64_t c0 = (blockIdx.x % tiles_c) * kTile;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+    constexpr bool PREV = KIND == PREP8_FISTA;
+#pragma unroll
+    for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+        const int64_t c = c0 + cc, r = r0 + tx;
+        if (c < W && r < R) {
+            sy1[cc][tx] = A.y[1][c * R + r];
+            if (PREV) sp1[cc][tx] = A.p[1][c * R + r];
+        }
+    }
+    for (int idx = threadIdx.x; idx < kTile * kZzWin; idx += kUpdThreads) {
+        const int cc = idx / kZzWin, qq = idx - cc * kZzWin;
+        const int64_t c = c0 + cc, q = r0 - 1 + qq;
+        if (c < W && q >= 0 && q < R) {
+            sy2[cc][qq] = A.y[2][c * R + q];
+            sy3[cc][qq] = A.y[3][c * R + q];
+            if (PREV) {
+                sp2[cc][qq] = A.p[2][c * R + q];
+                sp3[cc][qq] = A.p[3][c * R + q];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = ty; rr < kTile; rr += kUpdThreads / kTile) {
+        const int64_t r = r0 + rr, c = c0 + tx;
+        if (r >= R || c >= W) continue;
+        const int64_t g = r * W + c;
+        const int q2 = zz_row((int)r, (int)c, H, 2) - (int)(r0 - 1);
+        const int q3 = zz_row((int)r, (int)c, H, 3) - (int)(r0 - 1);
+        const T yv[4] = {A.y[0][g], sy1[tx][rr], sy2[tx][q2], sy3[tx][q3]};
+        const T wg = A.w[g];
+        if constexpr (KIND == PREP8_PRIMAL) {
+            T v = wg;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v -= yv[j];
+            A.xout[g] = v;
+        } else if constexpr (KIND == PREP8_BCD) {
+            T v = wg;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j != A.k) v -= yv[j];
+            // the result goes to block k's layout: staged in that block's buffer
+            if (A.k == 0) A.out[0][g] = v;
+            else if (A.k == 1) sp1[tx][rr] = v;
+            else if (A.k == 2) sp2[tx][q2] = v;
+            else sp3[tx][q3] = v;
+        } else {
+            const T pv[4] = {A.p[0][g], sp1[tx][rr], sp2[tx][q2], sp3[tx][q3]};
+            T u[4];
+            T usum = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                u[j] = yv[j] + A.beta * (yv[j] - pv[j]);
+                usum += u[j];
+            }
+            const T corr = (wg - usum) / T(4);
+            A.out[0][g] = u[0] + corr;
+            sp1[tx][rr] = u[1] + corr;         // every thread has read its own p values above
+            sp2[tx][q2] = u[2] + corr;
+            sp3[tx][q3] = u[3] + corr;
+        }
+    }
+    if constexpr (KIND != PREP8_PRIMAL) {
+        __syncthreads();
+        const bool all = KIND == PREP8_FISTA;
+        if (all || A.k == 1) {
+#pragma unroll
+            for (int cc = ty; cc < kTile; cc += kUpdThreads / kTile) {
+                const int64_t c = c0 + cc, r = r0 + tx;
+                if (c < W && r < R) A.out[1][c * R + r] = sp1[cc][tx];
+            }
+        }
+        if (all || A.k >= 2) {
+            for (int idx = threadIdx.x; idx < kTile * kZzWin; idx += kUpdThreads) {
+                const int cc = idx / kZzWin, qq = idx - cc * kZzWin;
+                const int64_t c = c0 + cc, q = r0 - 1 + qq;
+                if (c >= W || q < 0 || q >= R) continue;
+                const int64_t v2 = zz_row((int)q, (int)c, H, 2), v3 = zz_row((int)q, (int)c, H, 3);
+                if ((all || A.k == 2) && v2 >= r0 && v2 < r0 + kTile) A.out[2][c * R + q] = sp2[cc][qq];
+                if ((all || A.k == 3) && v3 >= r0 && v3 < r0 + kTile) A.out[3][c * R + q] = sp3[cc][qq];
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_prep8(int kind, const Prep8Args<T>& A, cudaStream_t s)
+{
+    const int64_t tiles = ((A.rows + kTile - 1) / kTile) * ((A.cols + kTile - 1) / kTile);
+    if (tiles == 0) return cudaSuccess;
+    const size_t smem = update8_smem<T>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(prep8_kernel<T, PREP8_BCD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(prep8_kernel<T, PREP8_PRIMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(prep8_kernel<T, PREP8_FISTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    if (kind == PREP8_BCD) prep8_kernel<T, PREP8_BCD><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    else if (kind == PREP8_PRIMAL) prep8_kernel<T, PREP8_PRIMAL><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    else prep8_kernel<T, PREP8_FISTA><<<(unsigned)tiles, kUpdThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
 #define TVCUT_SCAN_INST(T)                                                                  \
+    template cudaError_t launch_prep8<T>(int, const Prep8Args<T>&, cudaStream_t);           \
     template cudaError_t launch_update8<T>(int, const Update8Args<T>&, cudaStream_t);       \
     template cudaError_t launch_zz_weights<T>(const T*, const T*, T*, int, int, int, cudaStream_t); \
     template cudaError_t launch_zz_relayout<T>(const T*, T*, int, int, int, bool, cudaStream_t); \

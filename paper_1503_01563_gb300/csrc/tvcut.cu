@@ -151,8 +151,8 @@ static bool valid_params(const tvcut_params* p, std::string& why)
         why = "params.connectivity must be 0, 4, 6 or 8";
         return false;
     }
-    if (p->connectivity == 8 && ((p->algo != TVCUT_AAR && p->algo != TVCUT_AP) || (p->mapping >= 1 && p->mapping <= 4))) {
-        why = "connectivity 8 runs TVCUT_AAR or TVCUT_AP on the scan schedule (mapping -1, 0 or 5..9)";
+    if (p->connectivity == 8 && p->mapping >= 1 && p->mapping <= 4) {
+        why = "connectivity 8 runs on the scan schedule (mapping -1, 0 or 5..9)";
         return false;
     }
     return true;
@@ -456,12 +456,62 @@ static cudaError_t run_sweeps(tvcut_t h, int first, int mid, int last, int check
 // One iteration (or, with mode UPD_EVAL, only the primal of the current
 // state).  Scan schedule: one scan launch for all blocks + one update launch;
 // fused schedule (mapping 1..4): one sweep per block, the last one updating.
+template <typename T>
+static Prep8Args<T> prep8_args(tvcut_t h)
+{
+    Prep8Args<T> A;
+    memset(&A, 0, sizeof(A));
+    A.rows = h->dims[0];
+    A.cols = h->dims[1];
+    for (int j = 0; j < 4; ++j) A.y[j] = S_of<T>(h, j);
+    A.w = (const T*)h->w;
+    A.xout = X_of<T>(h);
+    return A;
+}
+
+// x = w - sum_k y_k of a state that holds the block duals (BCD, FISTA).
+template <typename T>
+static cudaError_t primal_of_duals(tvcut_t h)
+{
+    if (h->conn8) {
+        const Prep8Args<T> A = prep8_args<T>(h);
+        return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_prep8<T>(PREP8_PRIMAL, A, h->stream); });
+    }
+    UpdateArgs<T> U;
+    memset(&U, 0, sizeof(U));
+    U.rows = rows_of(h);
+    U.cols = cols_of(h);
+    U.r = h->ndim;
+    for (int k = 0; k < h->ndim; ++k) U.s[k] = S_of<T>(h, k);
+    U.w = (const T*)h->w;
+    U.xout = X_of<T>(h);
+    return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
+}
+
 // One cycle of block coordinate descent (Sec. 4.1, cyclic projections): for
 // k = 0..r-1, v = w - sum_{j != k} y_j, y_k = v - prox_{f_k}(v).  The state
 // holds the y_k; on check iterations the primal w - sum_k y_k goes to x.
 template <typename T>
 static cudaError_t run_bcd(tvcut_t h, int check)
 {
+    if (h->conn8) {                // four blocks; v_k in block k's own layout
+        for (int k = 0; k < 4; ++k) {
+            Prep8Args<T> A = prep8_args<T>(h);
+            A.k = k;
+            A.out[k] = P_of<T>(h);
+            cudaError_t e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_prep8<T>(PREP8_BCD, A, h->stream); });
+            if (e != cudaSuccess) return e;
+            ScanArgs<T> S;
+            memset(&S, 0, sizeof(S));
+            S.naxes = 1;
+            S.force = scan_force(h->p.mapping);
+            S.shadow = 1;
+            S.ax[0] = block_axis<T>(h, k, P_of<T>(h), S_of<T>(h, k));
+            e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
+            if (e != cudaSuccess) return e;
+        }
+        return check ? primal_of_duals<T>(h) : cudaSuccess;
+    }
     const int r = h->ndim;
     UpdateArgs<T> U;
     memset(&U, 0, sizeof(U));
@@ -497,21 +547,6 @@ static cudaError_t run_bcd(tvcut_t h, int check)
     return cudaSuccess;
 }
 
-// x = w - sum_k y_k of a state that holds the block duals (BCD, FISTA).
-template <typename T>
-static cudaError_t primal_of_duals(tvcut_t h)
-{
-    UpdateArgs<T> U;
-    memset(&U, 0, sizeof(U));
-    U.rows = rows_of(h);
-    U.cols = cols_of(h);
-    U.r = h->ndim;
-    for (int k = 0; k < h->ndim; ++k) U.s[k] = S_of<T>(h, k);
-    U.w = (const T*)h->w;
-    U.xout = X_of<T>(h);
-    return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_bcd_prepare<T>(U, -1, h->stream); });
-}
-
 // One FISTA step on the smooth dual (Sec. 4.1): v = Pi_L(y + beta (y - y_prev))
 // for all blocks, then y_prev <- Pi_K(v) by the scan (all blocks in one
 // launch, projection mode), then the two buffers swap so that the state holds
@@ -519,36 +554,39 @@ static cudaError_t primal_of_duals(tvcut_t h)
 template <typename T>
 static cudaError_t run_fista(tvcut_t h, int check)
 {
-    const int r = h->ndim;
-    FistaArgs<T> F;
-    memset(&F, 0, sizeof(F));
-    F.rows = rows_of(h);
-    F.cols = cols_of(h);
-    F.r = r;
-    F.beta = (T)((h->fista_tprev - 1.0) / h->fista_t);
-    for (int k = 0; k < r; ++k) {
-        F.y[k] = S_of<T>(h, k);
-        F.p[k] = (const T*)h->yprev + (int64_t)k * h->n;
-        F.v[k] = XK_of<T>(h, k);
+    const int r = h->nblk;
+    const T beta = (T)((h->fista_tprev - 1.0) / h->fista_t);
+    cudaError_t e;
+    if (h->conn8) {
+        Prep8Args<T> A = prep8_args<T>(h);
+        A.beta = beta;
+        for (int k = 0; k < 4; ++k) {
+            A.p[k] = (const T*)h->yprev + (int64_t)k * h->n;
+            A.out[k] = XK_of<T>(h, k);
+        }
+        e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_prep8<T>(PREP8_FISTA, A, h->stream); });
+    } else {
+        FistaArgs<T> F;
+        memset(&F, 0, sizeof(F));
+        F.rows = rows_of(h);
+        F.cols = cols_of(h);
+        F.r = r;
+        F.beta = beta;
+        for (int k = 0; k < r; ++k) {
+            F.y[k] = S_of<T>(h, k);
+            F.p[k] = (const T*)h->yprev + (int64_t)k * h->n;
+            F.v[k] = XK_of<T>(h, k);
+        }
+        F.w = (const T*)h->w;
+        e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_fista_prepare<T>(F, h->stream); });
     }
-    F.w = (const T*)h->w;
-    cudaError_t e = traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_fista_prepare<T>(F, h->stream); });
     if (e != cudaSuccess) return e;
     ScanArgs<T> S;
     memset(&S, 0, sizeof(S));
     S.naxes = r;
     S.force = scan_force(h->p.mapping);
     S.shadow = 1;
-    for (int k = 0; k < r; ++k) {
-        ChainGeom g = chain_geom(h->ndim, h->dims, k);
-        S.ax[k].nchains = g.nchains;
-        S.ax[k].inner = g.inner;
-        S.ax[k].m = g.m;
-        S.ax[k].transposed = k == r - 1 ? 1 : 0;
-        S.ax[k].v = XK_of<T>(h, k);
-        S.ax[k].a = (const T*)h->a[k];
-        S.ax[k].x = (T*)h->yprev + (int64_t)k * h->n;
-    }
+    for (int k = 0; k < r; ++k) S.ax[k] = block_axis<T>(h, k, XK_of<T>(h, k), (T*)h->yprev + (int64_t)k * h->n);
     e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
     if (e != cudaSuccess) return e;
     std::swap(h->state, h->yprev);

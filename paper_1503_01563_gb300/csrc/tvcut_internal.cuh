@@ -205,6 +205,26 @@ struct Update8Args {
 };
 template <typename T>
 cudaError_t launch_update8(int mode, const Update8Args<T>& args, cudaStream_t s);
+
+// Dual-iterate passes of an 8-connected grid (states hold y_k):
+//   PREP8_BCD:    v = w - sum_{j != k} y_j into out[k], in block k's layout;
+//   PREP8_PRIMAL: x = w - sum_j y_j into xout (grid layout);
+//   PREP8_FISTA:  out[j] = Pi_L(y + beta (y - p))_j for all four blocks.
+enum Prep8Kind : int { PREP8_BCD = 0, PREP8_PRIMAL = 1, PREP8_FISTA = 2 };
+template <typename T>
+struct Prep8Args {
+    int64_t rows;
+    int64_t cols;
+    int k;                 // PREP8_BCD: the block being updated
+    T beta;                // PREP8_FISTA
+    const T* y[4];
+    const T* p[4];         // PREP8_FISTA: previous iterate
+    T* out[4];
+    const T* w;
+    T* xout;
+};
+template <typename T>
+cudaError_t launch_prep8(int kind, const Prep8Args<T>& args, cudaStream_t s);
 // path weights of block 2 or 3 ((W-1) x H, element c of path q at c * H + q)
 // from the diagonal and anti-diagonal weights ((H-1) x (W-1), natural)
 template <typename T>

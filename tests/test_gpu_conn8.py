@@ -34,7 +34,7 @@ def rel_err(got, want):
 
 
 @pytest.mark.parametrize("dims", CASES)
-@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("algo", [0, 1, 2, 3])
 @pytest.mark.parametrize("mapping", [-1, 5, 6, 8])
 def test_conn8_iterations_f64(tv, c8, dims, algo, mapping):
     w, a = inputs.uniform_grid8(dims, 41)
@@ -44,15 +44,20 @@ def test_conn8_iterations_f64(tv, c8, dims, algo, mapping):
     done = 0
     for k in (1, 6, 17):
         s.iterate(k - done)
-        st, x = c8.iterate(algo, w, a, st, k - done)
+        if algo == 3:                  # FISTA: the oracle's momentum restarts per call, so run it from cold
+            st, x = c8.iterate(algo, w, a, c8.cold_state(algo, w), k)
+        else:
+            st, x = c8.iterate(algo, w, a, st, k - done)
         done = k
         assert rel_err(s.state(), st) < 1e-9, k
         assert rel_err(s.primal(), x) < 1e-9, k
+        if algo >= 2:
+            np.testing.assert_array_equal(s.dual(), s.state())
     s.close()
 
 
 @pytest.mark.parametrize("dims", [(64, 64), (37, 53)])
-@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("algo", [0, 1, 2, 3])
 def test_conn8_iterations_f32(tv, c8, dims, algo):
     w, a = inputs.uniform_grid8(dims, 42)
     s = tv.Solver(dims, algo=algo, dtype=tv.F32, check_every=1000, connectivity=8)
@@ -61,7 +66,10 @@ def test_conn8_iterations_f32(tv, c8, dims, algo):
     done = 0
     for k in (1, 10, 50):
         s.iterate(k - done)
-        st, x = c8.iterate(algo, w, a, st, k - done)
+        if algo == 3:
+            st, x = c8.iterate(algo, w, a, c8.cold_state(algo, w), k)
+        else:
+            st, x = c8.iterate(algo, w, a, st, k - done)
         done = k
         assert rel_err(s.primal(), x) < 1e-4, k
         assert rel_err(s.state(), st) < 1e-4, k
@@ -69,10 +77,11 @@ def test_conn8_iterations_f32(tv, c8, dims, algo):
 
 
 @pytest.mark.parametrize("dims", [(48, 40), (33, 17)])
-def test_conn8_exact_cut(tv, c8, dims):
+@pytest.mark.parametrize("algo", [0, 2, 3])
+def test_conn8_exact_cut(tv, c8, dims, algo):
     w, a = inputs.uniform_grid8(dims, 4)
     e_star = c8.maxflow(w, a)[1]
-    s = tv.Solver(dims, dtype=tv.F64, check_every=5, threshold=0.5 / w.size, connectivity=8)
+    s = tv.Solver(dims, algo=algo, dtype=tv.F64, check_every=5, threshold=0.5 / w.size, connectivity=8)
     s.set_problem(w, a)
     code, st = s.iterate(20000)
     assert code == tv.OK and st.certified
@@ -121,7 +130,7 @@ def test_conn8_state_roundtrip_and_dual(tv, c8):
 
 
 def test_conn8_errors(tv):
-    for kw in (dict(algo=2), dict(algo=3), dict(mapping=2)):
+    for kw in (dict(mapping=2), dict(mapping=4)):
         with pytest.raises(tv.TvcutError) as e:
             tv.Solver((8, 8), connectivity=8, **kw)
         assert e.value.code == tv.ERR_INVALID
