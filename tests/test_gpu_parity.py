@@ -336,3 +336,33 @@ def test_full_size_3d_volume(tv, orc):
     assert np.array_equal(lab, (x > np.float32(st.threshold)).astype(np.uint8))
     assert st.energy_i64 == int(orc.energy(w, a, lab))
     s.close()
+
+
+@pytest.mark.parametrize("dims", [(1, 70000), (70000, 1), (2, 30000), (1, 1, 9000), (3, 20000, 1)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_extreme_chain_lengths(tv, orc, dims, dtype):
+    """Chains longer than the lane-group scan's shared memory (they fall back
+    to one thread per chain) and single-row / single-column grids."""
+    w, a = inputs.uniform_grid(dims, 13)
+    code = tv.F64 if dtype == "f64" else tv.F32
+    s = tv.Solver(dims, dtype=code, check_every=1000)
+    s.set_problem(w, a)
+    s.iterate(5)
+    ref_s, ref_x = orc.iterate(0, w, a, orc.cold_state(0, w), 5)
+    tol = 1e-9 if dtype == "f64" else 1e-4
+    assert rel_err(s.state(), ref_s) < tol
+    assert rel_err(s.primal(), ref_x) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("dims", [(1, 70000), (2, 30000)])
+def test_extreme_chain_exact_cut(tv, orc, dims):
+    w, a = inputs.uniform_grid(dims, 14)
+    e_star = orc.maxflow(w, a)[1]
+    s = tv.Solver(dims, dtype=tv.F64, check_every=10, threshold=0.5 / w.size)
+    s.set_problem(w, a)
+    s.iterate(2000)                    # the oracle's iterates reach E* within 200 here
+    lab, st = s.cut()
+    assert st.energy_i64 == e_star
+    assert orc.energy(w, a, lab) == e_star
+    s.close()
