@@ -1,24 +1,30 @@
-// Iteration kernels of the product-space methods (Sec. 4.2-4.3).
+// Iteration kernels of the methods of Sec. 4.
 //
-// One iteration = one scan launch + one update launch:
+// AAR and AP: one iteration = one scan launch + one update launch:
 //
 //   scan:   x_k = prox_{f_k}(s_k) on every chain of every block k at once.
 //           The blocks' projections are independent in the product space
 //           (Sec. 4.2: Pi_K splits into the Pi_{K_k}), so all axes share one
-//           launch; one thread owns one chain.  The prox is the taut string of
-//           Sec. 3.2 in local form (see scan_chain).  Each block's state is
-//           stored so that consecutive chains are consecutive in memory
-//           ("chain-major"): the natural row-major layout already is for
-//           every axis but the last, and the last axis' block (rows) is kept
-//           transposed.  A warp's loads of one step are thus one 128-byte
-//           line.
+//           launch; a thread, or a group of 4-32 lanes, owns one chain.  The
+//           prox is the taut string of Sec. 3.2 in local form (see
+//           scan_chain).  Each block's state is stored so that consecutive
+//           chains are consecutive in memory ("chain-major"): the natural
+//           row-major layout already is for every axis but the last, the last
+//           axis' block (rows) is kept transposed, and the zig-zag path
+//           blocks of an 8-connected grid use the transposed layout with rows
+//           swapped within pairs.  A warp's loads of one step are thus one
+//           128-byte line.
 //
 //   update: per vertex, y_k = s_k - x_k and
 //             AAR (Eq. 3 with Eq. dualA): s_k <- y_k + (w - 2 sum y + sum s)/r
 //             AP  (Sec. 4.2):             s_k <- y_k + (w - sum y)/r
 //           and, on check iterations, the primal x = w - sum_k y_k (Sec. 2.3).
-//           Elementwise and coalesced; the transposed row block goes through
-//           32x32 shared-memory tiles.
+//           Elementwise and coalesced; the transposed blocks go through
+//           shared-memory tiles.
+//
+// BCD and FISTA (Sec. 4.1) hold the duals y_k; their passes form the point to
+// project (bcd_prepare_kernel, fista_prepare_kernel, prep8_kernel) and the
+// scan writes the projection v - prox(v) directly (SHADOW).
 #include "tvcut_internal.cuh"
 #include "taut_string.cuh"
 
@@ -63,11 +69,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
     scan_chain<T, SHADOW>(X.m, X.v + base, X.a + abase, X.x + base, stride);
 }
 
-// ---- warp-per-chain speculative scan ------------------------------------------
+// ---- lane-group (speculative pieces) scan -------------------------------------
 //
 // For few, long chains (a 2D grid has only H + W of them) one thread per chain
-// leaves the GPU idle, so a warp shares one chain: lane L scans piece L of 32
-// from a guessed state (a segment starts at the piece start with multiplier
+// leaves the GPU idle, so G lanes (4 .. 32, the kernel's template parameter)
+// share one chain: lane L scans piece L of G from a guessed state (a segment starts at the piece start with multiplier
 // 0; exact for lane 0) and records every bend it finds (position e and
 // direction).  After a bend at e the scan state is fixed (the next segment
 // starts at e+1 with multiplier +-a_e), so a lane's trajectory is the true one
@@ -301,7 +307,7 @@ template <typename T>
 cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
 {
     // one thread per chain unless the launch has too few chains to fill the
-    // GPU, in which case long chains go to the warp-per-chain scan (measured
+    // GPU, in which case long chains go to the lane-group scan (measured
     // on 256^3: 65,536 chains of 256 run faster as warps, 196,608 as threads)
     int64_t total = 0;
     for (int k = 0; k < A.naxes; ++k) total += A.ax[k].nchains;

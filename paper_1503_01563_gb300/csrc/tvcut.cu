@@ -1,14 +1,16 @@
 // C-ABI of tvcut (declared in include/tvcut.h): handle, device buffers and
-// the iteration driver of the product-space methods (Sec. 4.2-4.3).
+// the iteration driver of the methods of Sec. 4 (AAR, AP, BCD, FISTA).
 //
-// One iteration with r = ndim blocks is r chain sweeps (sweep.cu): sweeps
-// 0..r-2 project their block and accumulate a per-vertex running sum P; the
-// last sweep projects block r-1 and applies the reflection/averaging update
-// to every block state in the same pass.  With AAR (Eq. 3 and Eq. dualA),
+// With r blocks (one per axis, or four on an 8-connected 2D grid), AAR
+// (Eq. 3 and Eq. dualA) is
 //   z_k <- y_k + (w - 2 sum_j y_j + sum_j z_j) / r ,   y = Pi_K(z),
-// and with AP (Sec. 4.2), lambda_k <- y_k + (w - sum_j y_j) / r.  On check
-// iterations the last sweep also writes the primal x = w - sum_k y_k, which
-// the check kernels (aux.cu) threshold and evaluate.
+// and AP (Sec. 4.2) lambda_k <- y_k + (w - sum_j y_j) / r.  The default (scan)
+// schedule runs one scan launch over all blocks and one update launch
+// (scan.cu); the fused schedules (mapping 1-4, sweep.cu) run one sweep per
+// block, the last one updating every block state.  BCD and FISTA keep the
+// duals y and alternate a preparation pass with the scan in projection mode.
+// On check iterations the primal x = w - sum_k y_k is written for the check
+// kernels (aux.cu) to threshold and evaluate.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
