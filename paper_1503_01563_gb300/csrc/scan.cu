@@ -46,7 +46,12 @@ __device__ __forceinline__ void scan_cp_wait()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <typename T, bool SHADOW>
+// PADDED: every axis carries its weights in the state's layout (ap), so the
+// scan loads each element one step ahead (scan_chain_padded).  Used for the
+// prox output only: the projection-mode padded scan needs 48 registers, and
+// at 48 a 256^3 launch (196,608 chains, 10 CTAs of 128 per SM) no longer
+// fits the GPU in one wave; the compact scan needs 40.
+template <typename T, bool SHADOW, bool PADDED>
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
 {
     int k = 0;
@@ -66,7 +71,38 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs<T> A)
         abase = o * (int64_t)(X.m - 1) * X.inner + q;
         stride = X.inner;
     }
-    scan_chain<T, SHADOW>(X.m, X.v + base, X.a + abase, X.x + base, stride);
+    if constexpr (PADDED) scan_chain_padded<T, SHADOW>(X.m, X.v + base, X.ap + base, X.x + base, stride);
+    else scan_chain<T, SHADOW>(X.m, X.v + base, X.a + abase, X.x + base, stride);
+}
+
+template <typename T>
+__global__ void pad_weights_kernel(const T* __restrict__ a, T* __restrict__ ap, int64_t n, int64_t nchains,
+                                   int64_t inner, int m, int transposed)
+{
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j, src;
+        if (transposed) {                        // element j of chain c at j * nchains + c, both layouts
+            j = idx / nchains;
+            src = idx;
+        } else {                                 // chain (o, q): o * m * inner + j * inner + q, compact (m - 1)
+            const int64_t o = idx / ((int64_t)m * inner);
+            j = idx / inner - o * m;
+            src = idx - o * inner;
+        }
+        ap[idx] = j < m - 1 ? a[src] : T(0);
+    }
+}
+
+template <typename T>
+cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s)
+{
+    const int64_t n = X.nchains * (int64_t)X.m;
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pad_weights_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X.a, ap, n, X.nchains, X.inner, X.m, X.transposed);
+    return cudaGetLastError();
 }
 
 // ---- lane-group (speculative pieces) scan -------------------------------------
@@ -329,9 +365,16 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
             thr.ax[k].block_begin = blocks;
             blocks += (thr.ax[k].nchains + kScanThreads - 1) / kScanThreads;
         }
+        bool padded = !A.shadow;
+        for (int k = 0; k < thr.naxes; ++k) padded = padded && thr.ax[k].ap != nullptr;
         if (blocks > 0) {
-            if (A.shadow) scan_kernel<T, true><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
-            else scan_kernel<T, false><<<(unsigned)blocks, kScanThreads, 0, s>>>(thr);
+            const dim3 g((unsigned)blocks), b(kScanThreads);
+            if (padded) {
+                scan_kernel<T, false, true><<<g, b, 0, s>>>(thr);
+            } else {
+                if (A.shadow) scan_kernel<T, true, false><<<g, b, 0, s>>>(thr);
+                else scan_kernel<T, false, false><<<g, b, 0, s>>>(thr);
+            }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -922,6 +965,7 @@ cudaError_t launch_prep8(int kind, const Prep8Args<T>& A, cudaStream_t s)
     template cudaError_t launch_fista_prepare<T>(const FistaArgs<T>&, cudaStream_t);        \
     template cudaError_t launch_bcd_prepare<T>(const UpdateArgs<T>&, int, cudaStream_t);    \
     template cudaError_t launch_scan<T>(ScanArgs<T>, cudaStream_t);                         \
+    template cudaError_t launch_pad_weights<T>(const ScanAxis<T>&, T*, cudaStream_t);        \
     template cudaError_t launch_update<T>(int, const UpdateArgs<T>&, cudaStream_t);         \
     template cudaError_t launch_transpose<T>(const T*, T*, int64_t, int64_t, cudaStream_t);
 TVCUT_SCAN_INST(float)

@@ -101,6 +101,86 @@ __device__ __forceinline__ void scan_chain(int m, const T* __restrict__ v, const
     }
 }
 
+// scan_chain on padded weights: a holds one value per element, 0 at the
+// chain's last one (the state's own layout), so element i+1's value and
+// weight are loaded one step ahead with no bounds test on the weight.  The
+// loads of a step then overlap the arithmetic of the previous one; the
+// arithmetic and the order of the writes are those of scan_chain.
+template <typename T, bool SHADOW = false>
+__device__ __forceinline__ void scan_chain_padded(int m, const T* __restrict__ v, const T* __restrict__ a,
+                                                  T* __restrict__ x, int64_t stride)
+{
+    int s = 0, i = 0, ih = 0, il = 0;
+    T u0 = T(0), th = T(0), tl = T(0), uh = T(0), ul = T(0), ah = T(0), al = T(0);
+    const T* pv = v;
+    const T* pa = a;
+    T* px = x;                                   // next element to write
+    T cv = v[0], ca = a[0];                      // element i
+    for (;;) {
+        const T vi = cv;
+        const T Ai = ca;
+        T nv = T(0), na = T(0);                  // element i + 1
+        if (i + 1 < m) {
+            nv = pv[stride];
+            na = pa[stride];
+        }
+        bool init = (i == s);
+        if (!init) {
+            uh += th - vi;
+            ul += tl - vi;
+            const bool bhi = uh < -Ai;
+            const bool blo = !bhi && ul > Ai;
+            if (bhi || blo) {
+                const int e = bhi ? ih : il;
+                const T t = bhi ? th : tl;
+                u0 = bhi ? ah : -al;
+                for (int j = s; j <= e; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - t : t;
+                s = e + 1;
+                if (s < i) {
+                    i = s;
+                    pv = v + (int64_t)s * stride;
+                    pa = a + (int64_t)s * stride;
+                    cv = *pv;
+                    ca = *pa;
+                    continue;
+                }
+                init = true;
+            } else {
+                const int len = i - s + 1;
+                if (uh > Ai) {
+                    th -= div_len<T>(uh - Ai, len);
+                    uh = Ai;
+                    ih = i;
+                    ah = Ai;
+                }
+                if (ul < -Ai) {
+                    tl += div_len<T>(-Ai - ul, len);
+                    ul = -Ai;
+                    il = i;
+                    al = Ai;
+                }
+            }
+        }
+        if (init) {
+            th = vi + Ai - u0;
+            tl = vi - Ai - u0;
+            uh = Ai;
+            ul = -Ai;
+            ih = il = i;
+            ah = al = Ai;
+        }
+        if (i == m - 1) {
+            for (int j = s; j <= m - 1; ++j, px += stride) *px = SHADOW ? v[(int64_t)j * stride] - th : th;
+            break;
+        }
+        ++i;
+        pv += stride;
+        pa += stride;
+        cv = nv;
+        ca = na;
+    }
+}
+
 // The per-element step is written without branches except two rare ones
 // (writing a finished segment and restarting behind the current element), so
 // that the lanes of a warp, which bend, clamp and restart at different

@@ -37,6 +37,7 @@ struct tvcut_ctx {
     void* w = nullptr;             // n
     void* a[4] = {nullptr, nullptr, nullptr, nullptr};   // per block, in the block's layout
     int64_t a_len[4] = {0, 0, 0, 0};                      // input length per weight axis
+    void* ap[4] = {nullptr, nullptr, nullptr, nullptr};  // the same weights padded to the state's layout
     void* adiag = nullptr;         // 8-connected: diagonal / anti-diagonal weights, (H-1) x (W-1) row-major
     void* aanti = nullptr;
     void* scratch = nullptr;       // 2n: P | x  (also the staging area of host inputs)
@@ -117,6 +118,7 @@ extern "C" void tvcut_destroy(tvcut_t h)
     cudaFree(h->state);
     cudaFree(h->w);
     for (int k = 0; k < 4; ++k) cudaFree(h->a[k]);
+    for (int k = 0; k < 4; ++k) cudaFree(h->ap[k]);
     cudaFree(h->adiag);
     cudaFree(h->aanti);
     cudaFree(h->scratch);
@@ -210,6 +212,8 @@ extern "C" tvcut_status tvcut_create(int ndim, const int64_t* dims, const tvcut_
         if (e == cudaSuccess) e = cudaMalloc(&h->adiag, es * (size_t)(nd > 0 ? nd : 1));
         if (e == cudaSuccess) e = cudaMalloc(&h->aanti, es * (size_t)(nd > 0 ? nd : 1));
     }
+    // padded copies for the thread scan (the block-transposed schedule only)
+    for (int k = 0; k < nb && e == cudaSuccess && h->tlast; ++k) e = cudaMalloc(&h->ap[k], es * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch, es * (size_t)(2 * n));
     if (e == cudaSuccess) e = cudaMalloc(&h->xk, es * (size_t)(nb * n));
     if (e == cudaSuccess && prm.algo == TVCUT_FISTA) e = cudaMalloc(&h->yprev, es * (size_t)(nb * n));
@@ -285,6 +289,7 @@ static ScanAxis<T> block_axis(tvcut_t h, int k, const T* v, T* x)
     }
     X.v = v;
     X.a = (const T*)h->a[k];
+    X.ap = (const T*)h->ap[k];
     X.x = x;
     return X;
 }
@@ -537,6 +542,7 @@ static cudaError_t run_bcd(tvcut_t h, int check)
         S.ax[0].transposed = k == r - 1 ? 1 : 0;
         S.ax[0].v = P_of<T>(h);
         S.ax[0].a = (const T*)h->a[k];
+        if (S.ax[0].transposed == (block_layout(h, k) == 1 ? 1 : 0)) S.ax[0].ap = (const T*)h->ap[k];
         S.ax[0].x = S_of<T>(h, k);
         S.shadow = 1;                                     // y_k = v_k - prox(v_k)
         e = traced(h, TVCUT_K_PROX, 1, [&] { return launch_scan<T>(S, h->stream); });
@@ -805,11 +811,18 @@ static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dty
     if (st != TVCUT_OK) { h->have_a[axis] = false; return st; }
     if (h->tlast && axis == h->ndim - 1)
         CK(h, relayout<T>(h, (T*)h->a[axis], rows_of(h), cols_of(h) - 1, true), "tvcut_set_weights");
+    if (!diag && h->ap[axis])
+        CK(h, launch_pad_weights<T>(block_axis<T>(h, axis, nullptr, nullptr), (T*)h->ap[axis], h->stream),
+           "tvcut_set_weights");
     if (diag && (h->have_a[5 - axis] || h->a_len[axis] == 0)) {
-        for (int b = 2; b < 4; ++b)
+        for (int b = 2; b < 4; ++b) {
             CK(h, launch_zz_weights<T>((const T*)h->adiag, (const T*)h->aanti, (T*)h->a[b], (int)h->dims[0],
                                        (int)h->dims[1], b, h->stream),
                "tvcut_set_weights");
+            if (h->ap[b])
+                CK(h, launch_pad_weights<T>(block_axis<T>(h, b, nullptr, nullptr), (T*)h->ap[b], h->stream),
+                   "tvcut_set_weights");
+        }
     }
     h->have_a[axis] = true;
     h->int_a[axis] = dtype == TVCUT_I32;

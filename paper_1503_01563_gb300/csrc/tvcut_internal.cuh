@@ -31,7 +31,8 @@ struct ScanAxis {
     int m;
     int transposed;
     const T* v;
-    const T* a;
+    const T* a;            // compact weights (m - 1 per chain)
+    const T* ap;           // the same weights in the state's layout, 0 at each chain's end; may be null
     T* x;
 };
 
@@ -170,6 +171,10 @@ cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state,
 // Launchers (scan.cu)
 template <typename T>
 cudaError_t launch_scan(ScanArgs<T> args, cudaStream_t s);
+// ap[idx] = the weight after element idx of its chain, 0 at a chain's last
+// element, for every idx of a block stored as X describes (X.a compact).
+template <typename T>
+cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update(int mode, const UpdateArgs<T>& args, cudaStream_t s);
 template <typename T>
