@@ -433,7 +433,7 @@ def run_batch(args):
                           "iterate": "f32", "iters_per_step": iters,
                           "step": "cold start + iterations to the oracle-equal cut of the sampled grids + check",
                           "autotuned_scan": {"threads": chosen[0], "ctas_per_sm": chosen[1],
-                                             "predicated_step": chosen[2]},
+                                             "step": ["branchy", "predicated", "padded"][chosen[2]]},
                           "l2": "256 MB buffer written between steps; working set 3 GB > L2"},
                "time_to_oracle_equal_cut_ms": {"cold": ms_per_step if kstar else None, "warm": None},
                "iters_to_oracle_equal_cut": kstar, "sampled_grids_match": ok,

@@ -295,11 +295,19 @@ tvcut_status tvcut_batch_cut(tvcut_batch_t b, int g, uint8_t* labels, int space,
 tvcut_status tvcut_batch_get_state(tvcut_batch_t b, int g, void* s, int space);
 
 /* Time the chain-prox launch for CTA sizes {64, 128, 256}, {4, 8, 16} CTAs
- * per SM and the two forms of the scan step (with branches, or predicated so
- * that the lanes of a warp share one instruction stream) on the current
- * inputs and keep the fastest; chosen (may be NULL, else 3 ints) receives
- * {threads, ctas_per_sm, predicated}.  Results do not depend on it. */
+ * per SM and three forms of the scan step (0: with branches; 1: predicated,
+ * so that the lanes of a warp share one instruction stream; 2: with branches
+ * on weights padded to the state layout, each element loaded one step ahead)
+ * on the current inputs and keep the fastest; chosen (may be NULL, else 3
+ * ints) receives {threads, ctas_per_sm, step}.  The three steps do the same
+ * arithmetic, so results do not depend on the choice.  FISTA's projection
+ * scan takes step 0 when 2 is chosen. */
 tvcut_status tvcut_batch_autotune(tvcut_batch_t b, int* chosen);
+
+/* Set the chain-prox launch without timing (e.g. a choice saved from an
+ * earlier tvcut_batch_autotune): threads in {64, 128, 256}, ctas_per_sm in
+ * 1..32, step in {0, 1, 2} as above; anything else is TVCUT_ERR_INVALID. */
+tvcut_status tvcut_batch_set_launch(tvcut_batch_t b, int threads, int ctas_per_sm, int step);
 
 /* ---- Learned warm start -------------------------------------------------
  * A U-Net (4 levels, `base` channels at full resolution, 3x3 convolutions

@@ -74,6 +74,8 @@ struct BatchArgs {
     const T* w;
     const T* a0;
     const T* a1;
+    const T* ap0;     // a0 / a1 padded to the state layouts (0 at each chain's end)
+    const T* ap1;
     T* xout;
     uint8_t* labels;
     int* counter;     // work-item counter of the scan
@@ -88,7 +90,10 @@ struct BatchArgs {
     const T* best_level;      // per grid (labels pass)
 };
 
-template <typename T, bool PRED, bool SHADOW>
+// VAR: the chain scan's step: 0 branchy (scan_chain), 1 predicated
+// (scan_chain_predicated), 2 branchy on padded weights with each element
+// loaded a step ahead (scan_chain_padded; prox output only).
+template <typename T, int VAR, bool SHADOW>
 __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
 {
     __shared__ int item_s;
@@ -107,10 +112,12 @@ __global__ void __launch_bounds__(256) batch_scan_kernel(BatchArgs<T> A)
             const T* in = SHADOW ? (I.axis == 0 ? A.x0 : A.x1) : (I.axis == 0 ? A.s0 : A.s1);
             T* out = SHADOW ? (I.axis == 0 ? A.p0 : A.p1) : (I.axis == 0 ? A.x0 : A.x1);
             if (I.axis == 0) {        // column c: H elements, stride W (natural)
-                if (PRED) scan_chain_predicated<T, SHADOW>(D.H, in + b, A.a0 + D.aoff0 + c, out + b, D.W);
+                if constexpr (VAR == 2) scan_chain_padded<T, SHADOW>(D.H, in + b, A.ap0 + b, out + b, D.W);
+                else if constexpr (VAR == 1) scan_chain_predicated<T, SHADOW>(D.H, in + b, A.a0 + D.aoff0 + c, out + b, D.W);
                 else scan_chain<T, SHADOW>(D.H, in + b, A.a0 + D.aoff0 + c, out + b, D.W);
             } else {                  // row c: W elements, stride H (transposed)
-                if (PRED) scan_chain_predicated<T, SHADOW>(D.W, in + b, A.a1 + D.aoff1 + c, out + b, D.H);
+                if constexpr (VAR == 2) scan_chain_padded<T, SHADOW>(D.W, in + b, A.ap1 + b, out + b, D.H);
+                else if constexpr (VAR == 1) scan_chain_predicated<T, SHADOW>(D.W, in + b, A.a1 + D.aoff1 + c, out + b, D.H);
                 else scan_chain<T, SHADOW>(D.W, in + b, A.a1 + D.aoff1 + c, out + b, D.H);
             }
         }
@@ -413,6 +420,7 @@ struct tvcut_batch_ctx {
     int* d_first_row = nullptr;
     int* d_counter = nullptr;
     void *s0 = nullptr, *s1 = nullptr, *x0 = nullptr, *x1 = nullptr, *w = nullptr, *a0 = nullptr, *a1 = nullptr;
+    void *ap0 = nullptr, *ap1 = nullptr;  // a0 / a1 padded to the state layouts
     void *p0 = nullptr, *p1 = nullptr;   // FISTA: the other iterate buffers
     double* mom = nullptr;               // FISTA: t_{k-1}, t_k
     bool flip = false;                   // FISTA: the current iterate is in p0/p1
@@ -441,7 +449,7 @@ struct tvcut_batch_ctx {
     // launch configuration (autotuned)
     int scan_threads = 128;
     int scan_ctas_per_sm = 8;
-    int scan_predicated = 1;          // step variant of the chain scan
+    int scan_predicated = 1;          // step variant of the chain scan (VAR of batch_scan_kernel)
     int sms = 152;
     // graph cache
     cudaGraphExec_t graph = nullptr;
@@ -481,7 +489,7 @@ extern "C" void tvcut_batch_destroy(tvcut_batch_t b)
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void* ptrs[] = {b->d_grids, b->d_items, b->d_tiles, b->d_rows, b->d_first_row, b->d_counter, b->s0, b->s1,
-                    b->x0, b->x1, b->w, b->a0, b->a1, b->xout, b->stage, b->labels, b->levels, b->best,
+                    b->x0, b->x1, b->w, b->a0, b->a1, b->ap0, b->ap1, b->xout, b->stage, b->labels, b->levels, b->best,
                     b->partials, b->lpartials, b->gsum, b->glev, b->d_flags, b->d_absmax, b->p0, b->p1, b->mom};
     for (void* q : ptrs) cudaFree(q);
     delete b;
@@ -562,6 +570,8 @@ extern "C" tvcut_status tvcut_batch_create(int G, const int64_t* dims, const tvc
     A(&b->w, es * b->n);
     A(&b->a0, es * b->na0);
     A(&b->a1, es * b->na1);
+    A(&b->ap0, es * b->n);
+    A(&b->ap1, es * b->n);
     A(&b->xout, es * b->n);
     if (prm.algo == TVCUT_FISTA) {
         A(&b->p0, es * b->n);
@@ -633,6 +643,8 @@ static BatchArgs<T> args_of(tvcut_batch_t b)
     A.w = (const T*)b->w;
     A.a0 = (const T*)b->a0;
     A.a1 = (const T*)b->a1;
+    A.ap0 = (const T*)b->ap0;
+    A.ap1 = (const T*)b->ap1;
     A.xout = (T*)b->xout;
     A.labels = b->labels;
     A.counter = b->d_counter;
@@ -731,11 +743,30 @@ static tvcut_status bset_weights(tvcut_batch_t b, int g, int axis, const void* a
                              "tvcut_batch_set_weights");
         b->have_a0[g] = st == TVCUT_OK;
         b->int_a0[g] = dtype == TVCUT_I32;
+        if (st == TVCUT_OK) {             // columns: chain c's element j at j W + c, both layouts
+            ScanAxis<T> X;
+            memset(&X, 0, sizeof(X));
+            X.nchains = D.W;
+            X.inner = D.W;
+            X.m = D.H;
+            X.a = (const T*)b->a0 + D.aoff0;
+            BCK(b, launch_pad_weights<T>(X, (T*)b->ap0 + D.off, b->stream), "tvcut_batch_set_weights");
+        }
     } else {
         st = batch_ingest<T>(b, a, dtype, space, D.H, D.W - 1, true, true, (T*)b->a1 + D.aoff1, nullptr,
                              "tvcut_batch_set_weights");
         b->have_a1[g] = st == TVCUT_OK;
         b->int_a1[g] = dtype == TVCUT_I32;
+        if (st == TVCUT_OK) {             // rows: element j of row c at j H + c, both layouts
+            ScanAxis<T> X;
+            memset(&X, 0, sizeof(X));
+            X.nchains = D.H;
+            X.inner = 1;
+            X.m = D.W;
+            X.transposed = 1;
+            X.a = (const T*)b->a1 + D.aoff1;
+            BCK(b, launch_pad_weights<T>(X, (T*)b->ap1 + D.off, b->stream), "tvcut_batch_set_weights");
+        }
     }
     b->checked = false;
     drop_graph(b);
@@ -803,8 +834,8 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
             batch_fista_kernel<T, false><<<b->sms * 16, 256, 0, b->stream>>>(A);
             e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
             if (e != cudaSuccess) return e;
-            if (b->scan_predicated) batch_scan_kernel<T, true, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
-            else batch_scan_kernel<T, false, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            if (b->scan_predicated == 1) batch_scan_kernel<T, 1, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else batch_scan_kernel<T, 0, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             batch_momentum_kernel<<<1, 1, 0, b->stream>>>(b->mom);
             std::swap(A.s0, A.p0);                // the new iterate is where the scan wrote
             std::swap(A.s1, A.p1);
@@ -812,8 +843,9 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
         } else {
             e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
             if (e != cudaSuccess) return e;
-            if (b->scan_predicated) batch_scan_kernel<T, true, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
-            else batch_scan_kernel<T, false, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            if (b->scan_predicated == 2) batch_scan_kernel<T, 2, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else if (b->scan_predicated == 1) batch_scan_kernel<T, 1, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else batch_scan_kernel<T, 0, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             if (aar) batch_update_kernel<T, UPD_AAR><<<b->sms * 16, 256, 0, b->stream>>>(A);
             else batch_update_kernel<T, UPD_AP><<<b->sms * 16, 256, 0, b->stream>>>(A);
         }
@@ -1007,15 +1039,16 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
     const int per_sm[] = {4, 8, 16};
     float best = 1e30f;
     int bt = b->scan_threads, bp = b->scan_ctas_per_sm, bv = b->scan_predicated;
-    for (int pv = 0; pv < 2; ++pv)
+    for (int pv = 0; pv < 3; ++pv)
         for (int t : threads)
             for (int q : per_sm) {
                 float tot = 0.f;
                 for (int rep = 0; rep < 3; ++rep) {
                     BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream), "autotune");
                     BCK(b, cudaEventRecord(e0, b->stream), "autotune");
-                    if (pv) batch_scan_kernel<T, true, false><<<b->sms * q, t, 0, b->stream>>>(A);
-                    else batch_scan_kernel<T, false, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    if (pv == 2) batch_scan_kernel<T, 2, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    else if (pv == 1) batch_scan_kernel<T, 1, false><<<b->sms * q, t, 0, b->stream>>>(A);
+                    else batch_scan_kernel<T, 0, false><<<b->sms * q, t, 0, b->stream>>>(A);
                     BCK(b, cudaGetLastError(), "autotune");
                     BCK(b, cudaEventRecord(e1, b->stream), "autotune");
                     BCK(b, cudaEventSynchronize(e1), "autotune");
@@ -1040,6 +1073,19 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
         chosen[1] = bp;
         chosen[2] = bv;
     }
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_batch_set_launch(tvcut_batch_t b, int threads, int ctas_per_sm, int step)
+{
+    if (!b) return bfail(nullptr, TVCUT_ERR_INVALID, "tvcut_batch_set_launch: NULL handle");
+    if ((threads != 64 && threads != 128 && threads != 256) || ctas_per_sm < 1 || ctas_per_sm > 32 || step < 0 ||
+        step > 2)
+        return bfail(b, TVCUT_ERR_INVALID, "tvcut_batch_set_launch: threads 64/128/256, ctas_per_sm 1..32, step 0..2");
+    b->scan_threads = threads;
+    b->scan_ctas_per_sm = ctas_per_sm;
+    b->scan_predicated = step;
+    drop_graph(b);
     return TVCUT_OK;
 }
 

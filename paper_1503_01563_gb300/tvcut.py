@@ -30,7 +30,7 @@ EXPORTED = [
     "tvcut_project_chains", "tvcut_profile", "tvcut_profile_read", "tvcut_iterate_noalloc", "tvcut_get_dual",
     "tvcut_batch_create", "tvcut_batch_destroy", "tvcut_batch_last_error", "tvcut_batch_set_unary",
     "tvcut_batch_set_weights", "tvcut_batch_reset", "tvcut_batch_iterate", "tvcut_batch_cut",
-    "tvcut_batch_get_state", "tvcut_batch_autotune",
+    "tvcut_batch_get_state", "tvcut_batch_autotune", "tvcut_batch_set_launch",
     "tvcut_unet_create", "tvcut_unet_destroy", "tvcut_unet_last_error", "tvcut_unet_resize",
     "tvcut_unet_forward", "tvcut_unet_backward", "tvcut_unet_adam", "tvcut_unet_num_params",
     "tvcut_unet_get_params", "tvcut_unet_set_params", "tvcut_conv3x3_bf16", "tvcut_conv3x3_wgrad_bf16",
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "tvcut_batch_cut": (st, [P, c_int, P, c_int, ctypes.POINTER(Stats)]),
         "tvcut_batch_get_state": (st, [P, c_int, P, c_int]),
         "tvcut_batch_autotune": (st, [P, P]),
+        "tvcut_batch_set_launch": (st, [P, c_int, c_int, c_int]),
         "tvcut_unet_create": (st, [c_int, c_int, c_int, c_int, ctypes.c_uint64, P, ctypes.POINTER(P)]),
         "tvcut_unet_destroy": (None, [P]),
         "tvcut_unet_last_error": (ctypes.c_char_p, [P]),
@@ -443,6 +444,11 @@ class Batch:
         ch = (ctypes.c_int * 3)()
         _bcheck(lib().tvcut_batch_autotune(self.h, ch), self.h)
         return int(ch[0]), int(ch[1]), int(ch[2])
+
+    def set_launch(self, threads, ctas_per_sm, step):
+        """Chain-prox launch shape and step form (0 branchy, 1 predicated,
+        2 padded weights), e.g. a saved autotune result."""
+        _bcheck(lib().tvcut_batch_set_launch(self.h, int(threads), int(ctas_per_sm), int(step)), self.h)
 
 
 def _ucheck(code, u):

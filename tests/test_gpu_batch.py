@@ -106,11 +106,45 @@ def test_batch_autotune_keeps_results(tv):
     b.iterate(5)
     before = [b.state(g) for g in range(len(DIMS))]
     threads, per_sm, pred = b.autotune()
-    assert threads in (64, 128, 256) and per_sm in (4, 8, 16) and pred in (0, 1)
+    assert threads in (64, 128, 256) and per_sm in (4, 8, 16) and pred in (0, 1, 2)
     b.reset()
     b.iterate(5)
     for g in range(len(DIMS)):
         np.testing.assert_array_equal(b.state(g), before[g])
+
+
+@pytest.mark.parametrize("algo", [0, 1, 3])
+def test_batch_step_forms_agree(tv, orc, algo):
+    """The three forms of the scan step (branchy, predicated, padded weights
+    loaded a step ahead) give bit-identical iterates, within 1e-4 of the
+    FP64 oracle, for AAR, AP and FISTA (whose projection scan takes the
+    branchy step for form 2)."""
+    probs = problems(401)
+    out = []
+    for step in (0, 1, 2):
+        b = tv.Batch(DIMS, algo=algo, dtype=tv.F32)
+        for g, (w, a) in enumerate(probs):
+            b.set_problem(g, w, a)
+        b.set_launch(128, 8, step)
+        b.reset()
+        b.iterate(7)
+        out.append([b.state(g) for g in range(len(DIMS))])
+        b.close()
+    for g in range(len(DIMS)):
+        np.testing.assert_array_equal(out[1][g], out[0][g])
+        np.testing.assert_array_equal(out[2][g], out[0][g])
+    for g in (0, len(DIMS) - 1):
+        w, a = probs[g]
+        ref, _ = orc.iterate(algo, w, a, orc.cold_state(algo, w), 7)
+        assert np.abs(out[2][g] - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_batch_set_launch_rejects(tv):
+    b = tv.Batch([(4, 4), (3, 5)])
+    for bad in ((96, 8, 0), (128, 0, 0), (128, 33, 0), (128, 8, 3), (128, 8, -1)):
+        with pytest.raises(tv.TvcutError):
+            b.set_launch(*bad)
+    b.close()
 
 
 def test_batch_errors(tv):
