@@ -102,6 +102,14 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def scan_sources_sha256():
+    """Hash of the sources of the scan and update kernels (scan.cu, taut_string.cuh)."""
+    h = hashlib.sha256()
+    for f in ("scan.cu", "taut_string.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1503_01563_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(kind_name, workload):
     """DRAM bytes per launch of a kernel from a committed ncu summary, valid
     only while the iteration kernels' source is unchanged."""
@@ -109,9 +117,8 @@ def kernel_traffic(kind_name, workload):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = hashlib.sha256(open(os.path.join(ROOT, "paper_1503_01563_gb300", "csrc", "scan.cu"), "rb").read()).hexdigest()
     ent = d.get(workload, {}).get(kind_name)
-    if ent is None or d.get("scan_cu_sha256") != src:
+    if ent is None or d.get("scan_sources_sha256") != scan_sources_sha256():
         return None
     return ent
 
