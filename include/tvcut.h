@@ -353,11 +353,15 @@ tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dout, float* d
 
 /* tvcut_conv3x3_bf16 with the engine chosen: 0 automatic (what
  * tvcut_conv3x3_bf16 does), 1 the mma.sync kernel, 2 the tcgen05 kernel
- * (tensor memory accumulators, TMA-loaded operands; INVALID for shapes it
- * does not take: it needs Cin 16, 32 or a multiple of 64, Cout <= 256, W a
- * multiple of 128 or a divisor of 128, H*W a multiple of 128, 16-byte
- * aligned tensors).  Stream-ordered; a tcgen05 launch that gives up waiting
- * (2 s per wait) is reported by tvcut_conv_tc_error. */
+ * (tensor memory accumulators, TMA-loaded operands; persistent CTAs with
+ * the TMA producer, the MMA issuer and the epilogue in separate warps and
+ * two accumulator buffers, so that one tile's epilogue overlaps the next
+ * tile's loads and MMAs), 3 the tcgen05 kernel with one 128-pixel tile per
+ * CTA.  2 and 3 are INVALID for shapes the tcgen05 kernel does not take: it
+ * needs Cin 16, 32 or a multiple of 64, Cout <= 256, W a multiple of 128 or
+ * a divisor of 128, H*W a multiple of 128, 16-byte aligned tensors.
+ * Stream-ordered; a tcgen05 launch that gives up waiting (2 s per wait) is
+ * reported by tvcut_conv_tc_error. */
 tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, const float* bias, void* out,
                                    int N, int H, int W, int Cin, int Cout, int relu, int engine,
                                    void* cuda_stream);
@@ -368,8 +372,9 @@ tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, const float* 
 int tvcut_conv_tc_error(void);
 
 /* The U-Net's convolutions (forward and input gradient): engine 0 (default)
- * uses the tcgen05 kernel for every layer whose shape it takes and the
- * mma.sync kernel for the others; 1 uses the mma.sync kernel throughout. */
+ * uses the persistent tcgen05 kernel for every layer whose shape it takes
+ * and the mma.sync kernel for the others; 1 uses the mma.sync kernel
+ * throughout; 3 is 0 with the one-tile-per-CTA tcgen05 kernel. */
 tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine);
 
 /* Iterations without any device allocation.  The paper has no counterpart:

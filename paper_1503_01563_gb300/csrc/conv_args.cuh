@@ -23,7 +23,10 @@ struct ConvArgs {
 // tcgen05 implicit-GEMM convolution (conv_tc.cu): the shapes it takes, its
 // launch (cudaErrorNotSupported otherwise), and its give-up flag.
 bool conv_tc_supported(const ConvArgs& A);
-cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s);
+// form 0: persistent, warp-specialised, halo-loaded A operand where the
+// shape allows (default); 1: one 128-pixel tile per CTA; 2: persistent
+// without the halo form
+cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s, int form = 0);
 int conv_tc_take_error();
 
 }  // namespace nn

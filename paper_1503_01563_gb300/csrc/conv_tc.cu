@@ -262,6 +262,370 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const __grid_con
     }
 }
 
+// Persistent form: a CTA loops over tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... with its roles in separate warps, so that the loads and MMAs of the
+// next tile run while the epilogue drains the last one.
+//   warp 8 (one lane): TMA producer, one continuous stream of K blocks over
+//                      all of the CTA's tiles into the stage ring;
+//   warp 9 (one lane): MMA issuer, accumulating tile i into tensor-memory
+//                      buffer i % 2 (two buffers of ncols columns), then
+//                      committing to tfull[i % 2];
+//   warps 0-7:         epilogue of tile i from buffer i % 2: warp w reads
+//                      accumulator lanes 32 (w % 4) .. + 31 (the lane
+//                      quarter a warp may access) and the 16-column chunks
+//                      w / 4, w / 4 + 2, ...; then one arrival per warp on
+//                      tempty[i % 2] frees the buffer.
+// Every wait is bounded as in conv3x3_tc_kernel; after a give-up every role
+// stops at its next tile, and the CTA still frees its tensor memory.
+constexpr int TCP_EPI_WARPS = 8;
+constexpr int TCP_THREADS = 32 * (TCP_EPI_WARPS + 2);
+constexpr int TCP_MAX_CTAS = 3;
+
+__device__ __forceinline__ bool tc_failed() { return *(volatile int*)&g_conv_tc_error != 0; }
+
+__device__ __forceinline__ void tile_origin(const ConvArgs& A, int64_t t, int64_t& p0, int& img, int& y0, int& x0)
+{
+    const int64_t HW = (int64_t)A.H * A.W;
+    p0 = t * TC_M;
+    img = (int)(p0 / HW);
+    const int64_t rem = p0 - (int64_t)img * HW;
+    y0 = (int)(rem / A.W);
+    x0 = (int)(rem - (int64_t)y0 * A.W);
+}
+
+__global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const __grid_constant__ CUtensorMap tmB,
+                                                                  ConvArgs A, TcShape S, int64_t tiles)
+{
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const int stage_bytes = S.a_bytes + S.b_bytes;
+    uint64_t* full = (uint64_t*)(sm + (size_t)S.stages * stage_bytes);
+    uint64_t* empty = full + S.stages;
+    uint64_t* tfull = empty + S.stages;      // [2]
+    uint64_t* tempty = tfull + 2;            // [2]
+    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < S.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TCP_EPI_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(2 * S.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == TCP_EPI_WARPS) {
+        if (lane == 0) {
+            int64_t kbg = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < tiles && ok && !tc_failed(); t += gridDim.x) {
+                int64_t p0;
+                int img, y0, x0;
+                tile_origin(A, t, p0, img, y0, x0);
+                for (int kb = 0; kb < S.kblocks; ++kb, ++kbg) {
+                    const int s = (int)(kbg % S.stages);
+                    const int64_t use = kbg / S.stages;
+                    if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = kb / S.chunks, c0 = (kb - tap * S.chunks) * S.cblk;
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+                    uint8_t* sa = sm + (size_t)s * stage_bytes;
+                    mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+                    tma_load_4d(sa, &tmA, c0, x0 + kx - 1, y0 + ky - 1, img, &full[s]);
+                    tma_load_3d(sa + S.a_bytes, &tmB, c0, 0, tap, &full[s]);
+                }
+            }
+        }
+    } else if (warp == TCP_EPI_WARPS + 1) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(A.Cout >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            const uint32_t row_bytes = (uint32_t)S.cblk * 2u;
+            int64_t kbg = 0;
+            int it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < tiles && ok && !tc_failed(); t += gridDim.x, ++it) {
+                const int buf = it & 1, ubuf = it >> 1;
+                if (ubuf > 0 && !mbar_wait(&tempty[buf], (uint32_t)((ubuf - 1) & 1))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * S.ncols);
+                for (int kb = 0; kb < S.kblocks; ++kb, ++kbg) {
+                    const int s = (int)(kbg % S.stages);
+                    const int64_t use = kbg / S.stages;
+                    if (!mbar_wait(&full[s], (uint32_t)(use & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes);
+                    const uint64_t ad = smem_desc(sa, row_bytes, (uint32_t)S.swz);
+                    const uint64_t bd = smem_desc(sa + (uint32_t)S.a_bytes, row_bytes, (uint32_t)S.swz);
+                    for (int k = 0; k < S.cblk / 16; ++k)
+                        mma_bf16_ss(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kb | k) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1, ubuf = it >> 1;
+            const bool have = mbar_wait(&tfull[buf], (uint32_t)(ubuf & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!__all_sync(0xffffffffu, have && !tc_failed())) break;   // warp-uniform: tcgen05.ld is .aligned
+            int64_t p0;
+            int img, y0, x0;
+            tile_origin(A, t, p0, img, y0, x0);
+            const int q = warp & 3;
+            const int m = q * 32 + lane;
+            const int64_t p = p0 + m;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S.ncols);
+            for (int c = (warp >> 2) * 16; c < A.Cout; c += 16 * (TCP_EPI_WARPS / 4)) {
+                uint32_t r[16];
+                tmem_ld16(trow + (uint32_t)c, r);
+                const int64_t o = p * A.CoutStride + c;
+                __align__(16) __nv_bfloat16 ob[16];
+                __align__(16) __nv_bfloat16 mk[16];
+                __align__(16) float bs[16];
+                if (A.mask) {
+                    *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
+                    *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
+                }
+                if (A.bias) {
+                    if (((uintptr_t)A.bias & 15) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) *(float4*)&bs[j] = *(const float4*)(A.bias + c + j);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) bs[j] = A.bias[c + j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float v = __uint_as_float(r[j]);
+                    if (A.bias) v += bs[j];
+                    if (A.relu) v = fmaxf(v, 0.f);
+                    if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
+                    ob[j] = __float2bfloat16(v);
+                    if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
+                }
+                *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
+                *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * S.ncols)
+                     : "memory");
+    }
+}
+
+// Halo form (Cin 16, 32 or 64, tiles inside one image row): per tile one
+// TMA box per 8-channel chunk brings the three input rows the tile's taps
+// read, 130 pixels wide (the tile and one pixel on each side; zero fill at
+// the image border), in the canonical K-major layout without swizzle:
+// [chunk][row][pixel][8 channels].  The A operand of tap (ky, kx) is then
+// the same buffer started ky rows and kx pixels further (16-byte steps of
+// the descriptor's start address), so the nine taps need no further loads.
+// The weights of all nine taps stay resident in shared memory for the CTA's
+// life ([tap][chunk][cout][8]).  Roles, tensor-memory buffers and bounded
+// waits are those of conv3x3_tcp_kernel.
+constexpr int HALO_W = TC_M + 2;
+
+struct HaloShape {
+    int kch;         // Cin / 8
+    int kstride;     // bytes of one chunk's three halo rows (128-byte multiple)
+    int slot_bytes;  // kch * kstride
+    int slots;
+    int w_bytes;     // 9 * kch * Cout * 16
+    int ncols;
+};
+
+__device__ __forceinline__ uint64_t smem_desc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;   // next 8-element group along K
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;   // next 8 rows
+    d |= (uint64_t)1 << 46;                          // descriptor version; layout 0: no swizzle
+    return d;
+}
+
+__global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(const __grid_constant__ CUtensorMap tmH,
+                                                                               const __grid_constant__ CUtensorMap tmW,
+                                                                               ConvArgs A, HaloShape S, int64_t tiles)
+{
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint8_t* wsm = sm;                                   // resident weights
+    uint8_t* hsm = sm + S.w_bytes;                       // halo slots
+    uint64_t* wbar = (uint64_t*)(hsm + (size_t)S.slots * S.slot_bytes);
+    uint64_t* full = wbar + 1;
+    uint64_t* empty = full + S.slots;
+    uint64_t* tfull = empty + S.slots;                   // [2]
+    uint64_t* tempty = tfull + 2;                        // [2]
+    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        mbar_init(wbar, 1);
+        for (int s = 0; s < S.slots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TCP_EPI_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(2 * S.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const int wchunk = A.Cout * 16;                      // bytes of one (tap, chunk) weight box
+
+    if (warp == TCP_EPI_WARPS) {
+        if (lane == 0) {
+            mbar_expect_tx(wbar, (uint32_t)S.w_bytes);
+            for (int t = 0; t < 9; ++t)
+                for (int kc = 0; kc < S.kch; ++kc)
+                    tma_load_3d(wsm + (size_t)(t * S.kch + kc) * wchunk, &tmW, 8 * kc, 0, t, wbar);
+            int64_t it = 0;
+            for (int64_t t = blockIdx.x; t < tiles && !tc_failed(); t += gridDim.x, ++it) {
+                const int s = (int)(it % S.slots);
+                const int64_t use = it / S.slots;
+                if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) break;
+                int64_t p0;
+                int img, y0, x0;
+                tile_origin(A, t, p0, img, y0, x0);
+                uint8_t* slot = hsm + (size_t)s * S.slot_bytes;
+                mbar_expect_tx(&full[s], (uint32_t)(S.kch * 3 * HALO_W * 16));
+                for (int kc = 0; kc < S.kch; ++kc)
+                    tma_load_4d(slot + (size_t)kc * S.kstride, &tmH, 8 * kc, x0 - 1, y0 - 1, img, &full[s]);
+            }
+        }
+    } else if (warp == TCP_EPI_WARPS + 1) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(A.Cout >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            bool ok = mbar_wait(wbar, 0);
+            const uint32_t wbase = smem_u32(wsm);
+            int64_t it = 0;
+            for (int64_t t = blockIdx.x; t < tiles && ok && !tc_failed(); t += gridDim.x, ++it) {
+                const int buf = (int)(it & 1);
+                const int64_t ubuf = it >> 1;
+                if (ubuf > 0 && !mbar_wait(&tempty[buf], (uint32_t)((ubuf - 1) & 1))) break;
+                const int s = (int)(it % S.slots);
+                const int64_t use = it / S.slots;
+                if (!mbar_wait(&full[s], (uint32_t)(use & 1))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * S.ncols);
+                const uint32_t hbase = smem_u32(hsm + (size_t)s * S.slot_bytes);
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+                    for (int h = 0; h < S.kch / 2; ++h) {
+                        const uint32_t sa = hbase + (uint32_t)(2 * h * S.kstride) + (uint32_t)((ky * HALO_W + kx) * 16);
+                        const uint32_t sb = wbase + (uint32_t)((tap * S.kch + 2 * h) * wchunk);
+                        mma_bf16_ss(d, smem_desc_plain(sa, (uint32_t)S.kstride, 128u),
+                                    smem_desc_plain(sb, (uint32_t)wchunk, 128u), idesc, (tap | h) ? 1u : 0u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1, ubuf = it >> 1;
+            const bool have = mbar_wait(&tfull[buf], (uint32_t)(ubuf & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!__all_sync(0xffffffffu, have && !tc_failed())) break;
+            int64_t p0;
+            int img, y0, x0;
+            tile_origin(A, t, p0, img, y0, x0);
+            const int q = warp & 3;
+            const int64_t p = p0 + q * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S.ncols);
+            for (int c = (warp >> 2) * 16; c < A.Cout; c += 16 * (TCP_EPI_WARPS / 4)) {
+                uint32_t r[16];
+                tmem_ld16(trow + (uint32_t)c, r);
+                const int64_t o = p * A.CoutStride + c;
+                __align__(16) __nv_bfloat16 ob[16];
+                __align__(16) __nv_bfloat16 mk[16];
+                __align__(16) float bs[16];
+                if (A.mask) {
+                    *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
+                    *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
+                }
+                if (A.bias) {
+                    if (((uintptr_t)A.bias & 15) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) *(float4*)&bs[j] = *(const float4*)(A.bias + c + j);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) bs[j] = A.bias[c + j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float v = __uint_as_float(r[j]);
+                    if (A.bias) v += bs[j];
+                    if (A.relu) v = fmaxf(v, 0.f);
+                    if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
+                    ob[j] = __float2bfloat16(v);
+                    if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
+                }
+                *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
+                *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * S.ncols)
+                     : "memory");
+    }
+}
+
 // ---- host ---------------------------------------------------------------------
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -325,14 +689,132 @@ static TcShape tc_shape(const ConvArgs& A)
 
 static size_t tc_smem(const TcShape& S)
 {
-    return 1024 + (size_t)S.stages * (S.a_bytes + S.b_bytes) + (size_t)(2 * S.stages + 1) * 8 + 16;
+    return 1024 + (size_t)S.stages * (S.a_bytes + S.b_bytes) + (size_t)(2 * S.stages + 4) * 8 + 16;
 }
 
-cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s)
+// Persistent form: CTAs per SM as tensor memory allows (two accumulator
+// buffers of ncols columns each, 512 columns per SM), at most 3, sharing a
+// stage ring budget of 192 KB per SM, deep enough to keep the few-channel
+// layers' loads streaming across tiles.
+static int tcp_ctas_per_sm(const TcShape& S)
+{
+    const int c = 512 / (2 * S.ncols);
+    return c < TCP_MAX_CTAS ? c : TCP_MAX_CTAS;
+}
+
+static TcShape tcp_shape(const ConvArgs& A)
+{
+    TcShape S = tc_shape(A);
+    const int stage = S.a_bytes + S.b_bytes;
+    const int ring = 192 * 1024 / tcp_ctas_per_sm(S);
+    int st = ring / stage;
+    if (st < 2) st = 2;
+    if (st > 32) st = 32;
+    S.stages = st;
+    return S;
+}
+
+static int sm_count()
+{
+    static int dev_cached = -1, n = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != dev_cached) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+        dev_cached = dev;
+    }
+    return n;
+}
+
+// Halo form: Cin 16, 32 or 64, tiles inside one image row, the nine taps'
+// weights at most 48 KB, and at least two CTAs per SM with at least two halo
+// slots each (at most 6) within tensor memory and a 216 KB shared-memory
+// budget.  With one CTA per SM the form was slower than the others
+// (2048^2, 64 -> 32 channels: 619 us against 357-390 us).
+static bool tch_shape(const ConvArgs& A, HaloShape& S, int& cps)
+{
+    if (!(A.Cin == 16 || A.Cin == 32 || A.Cin == 64) || A.W % TC_M) return false;
+    S.kch = A.Cin / 8;
+    S.kstride = ((3 * HALO_W * 16 + 127) / 128) * 128;
+    S.slot_bytes = S.kch * S.kstride;
+    S.w_bytes = 9 * S.kch * A.Cout * 16;
+    if (S.w_bytes > 48 * 1024) return false;
+    int nc = 32;
+    while (nc < A.Cout) nc <<= 1;
+    S.ncols = nc;
+    cps = 512 / (2 * nc);
+    if (cps > TCP_MAX_CTAS) cps = TCP_MAX_CTAS;
+    for (; cps >= 2; --cps) {
+        const int budget = 216 * 1024 / cps - 1024 - 256 - S.w_bytes;
+        int sl = budget / S.slot_bytes;
+        if (sl > 6) sl = 6;
+        if (sl >= 2) {
+            S.slots = sl;
+            return true;
+        }
+    }
+    return false;
+}
+
+static size_t tch_smem(const HaloShape& S)
+{
+    return 1024 + (size_t)S.w_bytes + (size_t)S.slots * S.slot_bytes + (size_t)(1 + 2 * S.slots + 4) * 8 + 16;
+}
+
+static cudaError_t launch_tch(const ConvArgs& A, const HaloShape& S, int cps, cudaStream_t s)
+{
+    EncodeTiledFn enc = encode_fn();
+    alignas(64) CUtensorMap tmH, tmW;
+    {   // activations (C, W, H, N); box: 8 channels x 130 pixels x 3 rows
+        const cuuint64_t dims[4] = {(cuuint64_t)A.Cin, (cuuint64_t)A.W, (cuuint64_t)A.H, (cuuint64_t)A.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)A.Cin * 2, (cuuint64_t)A.W * A.Cin * 2,
+                                       (cuuint64_t)A.H * A.W * A.Cin * 2};
+        const cuuint32_t box[4] = {8, (cuuint32_t)HALO_W, 3, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)A.in, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {   // weights [9][Cout][Cin]: dims (Cin, Cout, 9); box: 8 channels x Cout
+        const cuuint64_t dims[3] = {(cuuint64_t)A.Cin, (cuuint64_t)A.Cout, 9};
+        const cuuint64_t strides[2] = {(cuuint64_t)A.Cin * 2, (cuuint64_t)A.Cout * A.Cin * 2};
+        const cuuint32_t box[3] = {8, (cuuint32_t)A.Cout, 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)A.wt, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(conv3x3_tch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorInvalidDevice;
+    const int64_t tiles = (int64_t)A.N * A.H * A.W / TC_M;
+    int64_t grid = (int64_t)sms * cps;
+    if (grid > tiles) grid = tiles;
+    conv3x3_tch_kernel<<<(unsigned)grid, TCP_THREADS, tch_smem(S), s>>>(tmH, tmW, A, S, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s, int form)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc || !conv_tc_supported(A)) return cudaErrorNotSupported;
-    const TcShape S = tc_shape(A);
+    if (form == 0) {
+        HaloShape H;
+        int cps = 0;
+        if (tch_shape(A, H, cps)) return launch_tch(A, H, cps, s);
+    }
+    const bool persistent = form == 0 || form == 2;
+    const TcShape S = persistent ? tcp_shape(A) : tc_shape(A);
     const CUtensorMapSwizzle swz = S.cblk == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
                                    : S.cblk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                   : CU_TENSOR_MAP_SWIZZLE_128B;
@@ -367,11 +849,21 @@ cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s)
     if (e != cudaSuccess) return e;
     if (attr_dev != dev) {
         e = cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv3x3_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
     const int64_t tiles = (int64_t)A.N * A.H * A.W / TC_M;
-    conv3x3_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, s>>>(tmA, tmB, A, S);
+    if (persistent) {
+        const int sms = sm_count();
+        if (sms <= 0) return cudaErrorInvalidDevice;
+        int64_t grid = (int64_t)sms * tcp_ctas_per_sm(S);
+        if (grid > tiles) grid = tiles;
+        conv3x3_tcp_kernel<<<(unsigned)grid, TCP_THREADS, smem, s>>>(tmA, tmB, A, S, tiles);
+    } else {
+        conv3x3_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, s>>>(tmA, tmB, A, S);
+    }
     return cudaGetLastError();
 }
 

@@ -476,11 +476,13 @@ extern "C" tvcut_status tvcut_unet_resize(tvcut_unet_t u, int N, int H, int W)
     return alloc_acts(u, N, H, W);
 }
 
-// A 3x3 convolution: the tcgen05 kernel when the shape allows it (engine 0),
-// else the mma.sync kernel.
+// A 3x3 convolution: the tcgen05 kernel when the shape allows it (engine 0:
+// its persistent forms; 3: one tile per CTA; 4: persistent without the halo
+// form), else the mma.sync kernel.
 static cudaError_t launch_conv(const ConvArgs& A, int engine, cudaStream_t s)
 {
-    if (engine != 1 && conv_tc_supported(A)) return launch_conv3x3_tc(A, s);
+    if (engine != 1 && conv_tc_supported(A))
+        return launch_conv3x3_tc(A, s, engine == 3 ? 1 : engine == 4 ? 2 : 0);
     const int64_t P = (int64_t)A.N * A.H * A.W;
     dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((A.Cout + BN - 1) / BN));
     conv3x3_fwd_kernel<<<grid, FTHREADS, 0, s>>>(A);
@@ -757,7 +759,7 @@ extern "C" tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, co
 {
     if (!in || !wt || !out || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 16 || Cin < 16 || Cout < 16)
         return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16: bad arguments (channels multiples of 16)");
-    if (engine < 0 || engine > 2) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16_ex: engine must be 0, 1 or 2");
+    if (engine < 0 || engine > 4) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16_ex: engine must be 0..4");
     ConvArgs A;
     A.in = (const bf16*)in;
     A.wt = (const bf16*)wt;
@@ -772,9 +774,9 @@ extern "C" tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, co
     A.Cout = Cout;
     A.CoutStride = Cout;
     A.relu = relu;
-    if (engine == 2 && !conv_tc_supported(A))
+    if (engine >= 2 && !conv_tc_supported(A))
         return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_conv3x3_bf16_ex: shape not supported by the tcgen05 kernel");
-    cudaError_t e = launch_conv(A, engine == 1 ? 1 : 0, (cudaStream_t)stream);
+    cudaError_t e = launch_conv(A, engine == 2 ? 0 : engine, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return ufail(nullptr, TVCUT_ERR_CUDA, cudaGetErrorString(e));
@@ -809,7 +811,8 @@ extern "C" tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dou
 extern "C" tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine)
 {
     if (!u) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_unet_set_engine: NULL handle");
-    if (engine != 0 && engine != 1) return ufail(u, TVCUT_ERR_INVALID, "tvcut_unet_set_engine: engine must be 0 or 1");
+    if (engine != 0 && engine != 1 && engine != 3 && engine != 4)
+        return ufail(u, TVCUT_ERR_INVALID, "tvcut_unet_set_engine: engine must be 0, 1, 3 or 4");
     u->engine = engine;
     return TVCUT_OK;
 }

@@ -78,7 +78,7 @@ def test_conv_tcgen05(tv, shape, relu):
     wd = torch.tensor(wk).to(torch.bfloat16).cuda()
     bd = torch.tensor(b).cuda()
     outs = []
-    for engine in (2, 1):
+    for engine in (2, 1, 3, 4):
         out = torch.full((n, h, w, co), 7.0, dtype=torch.bfloat16, device="cuda")
         code = tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(),
                                               n, h, w, ci, co, relu, engine, None)
@@ -86,6 +86,10 @@ def test_conv_tcgen05(tv, shape, relu):
         torch.cuda.synchronize()
         outs.append(out.float().cpu().numpy())
     assert tv.lib().tvcut_conv_tc_error() == 0
+    # the persistent (halo or not) and the one-tile-per-CTA forms run the same
+    # MMAs in the same order
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[3], outs[2])
     Wt = torch.tensor(wk).reshape(3, 3, co, ci).permute(2, 3, 0, 1)
     xt = torch.tensor(x).permute(0, 3, 1, 2)
     ref = unet_ref.F.conv2d(xt, Wt, torch.tensor(b), padding=1).permute(0, 2, 3, 1)
@@ -96,6 +100,35 @@ def test_conv_tcgen05(tv, shape, relu):
     assert rel(outs[0], outs[1]) < 1e-2
     # rounding only: no output differs by more than a few BF16 steps of its magnitude
     assert np.all(np.abs(outs[0] - outs[1]) <= 2 ** -6 * np.maximum(np.abs(outs[1]), 1.0))
+
+
+@pytest.mark.parametrize("shape", [(1, 512, 512, 16, 32), (2, 256, 256, 64, 256), (4, 64, 128, 32, 64),
+                                   (1, 1024, 64, 128, 128), (3, 96, 256, 256, 16), (1, 256, 256, 64, 32),
+                                   (2, 64, 384, 32, 48), (1, 128, 128, 16, 16)])
+def test_conv_tcgen05_persistent_many_tiles(tv, shape):
+    """Shapes with several tiles per persistent CTA, so that both tensor-memory
+    accumulator buffers and the stage or halo ring are reused many times: the
+    persistent forms (engine 2, with the halo-loaded operand where the shape
+    allows; engine 4 without it) equal the one-tile-per-CTA form (engine 3)
+    bit for bit and the mma.sync kernel (engine 1) up to rounding."""
+    n, h, w, ci, co = shape
+    g = torch.Generator(device="cuda").manual_seed(sum(shape))
+    xd = torch.randn((n, h, w, ci), generator=g, device="cuda").to(torch.bfloat16)
+    wd = (torch.randn((9, co, ci), generator=g, device="cuda") * (0.6 / ci ** 0.5)).to(torch.bfloat16)
+    bd = torch.randn((co,), generator=g, device="cuda")
+    outs = []
+    for engine in (2, 3, 1, 4):
+        out = torch.full((n, h, w, co), 7.0, dtype=torch.bfloat16, device="cuda")
+        code = tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(),
+                                              n, h, w, ci, co, 1, engine, None)
+        assert code == tv.OK
+        torch.cuda.synchronize()
+        outs.append(out.float())
+    assert tv.lib().tvcut_conv_tc_error() == 0
+    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[3], outs[1])
+    d = (outs[0] - outs[2]).abs()
+    assert bool((d <= 2 ** -6 * torch.clamp(outs[2].abs(), min=1.0)).all())
 
 
 def test_conv_tcgen05_rejects_other_shapes(tv):
@@ -122,12 +155,15 @@ def test_network_engines_agree(tv):
     x = torch.tensor(rng.normal(size=(n, h, w, 3)).astype(np.float32)).cuda()
     t = torch.tensor(rng.normal(size=(n, h, w, 2)).astype(np.float32)).cuda()
     res = []
-    for engine in (0, 1):
+    for engine in (0, 1, 3):
         net.set_engine(engine)
         out = net.forward(x).cpu().numpy()
         loss = net.backward(t)
         res.append((out, loss, net.params(which=1)))
     assert tv.lib().tvcut_conv_tc_error() == 0
+    np.testing.assert_array_equal(res[0][0], res[2][0])
+    # the weight gradient's kernel accumulates with atomics: equal up to summation order
+    assert rel(res[0][2], res[2][2]) < 1e-5
     assert rel(res[0][0], res[1][0]) < 1e-2
     assert abs(res[0][1] - res[1][1]) < 1e-2 * res[1][1]
     assert rel(res[0][2], res[1][2]) < 5e-2
