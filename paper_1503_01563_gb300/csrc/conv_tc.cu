@@ -453,8 +453,10 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tcp_kernel(
 // the same buffer started ky rows and kx pixels further (16-byte steps of
 // the descriptor's start address), so the nine taps need no further loads.
 // The weights of all nine taps stay resident in shared memory for the CTA's
-// life ([tap][chunk][cout][8]).  Roles, tensor-memory buffers and bounded
-// waits are those of conv3x3_tcp_kernel.
+// life ([tap][chunk][cout][8]).  Roles and bounded waits are those of
+// conv3x3_tcp_kernel; where tensor memory holds four accumulator buffers
+// per CTA, the eight epilogue warps form two groups of four that drain
+// alternate tiles (buffers i % 4), so that two tiles' epilogues overlap.
 constexpr int HALO_W = TC_M + 2;
 
 struct HaloShape {
@@ -464,6 +466,8 @@ struct HaloShape {
     int slots;
     int w_bytes;     // 9 * kch * Cout * 16
     int ncols;
+    int groups;      // epilogue groups (1 or 2): group g drains tiles i with i % groups == g
+    int nbuf;        // tensor-memory accumulator buffers: 2 per group
 };
 
 __device__ __forceinline__ uint64_t smem_desc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -487,10 +491,11 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
     uint64_t* wbar = (uint64_t*)(hsm + (size_t)S.slots * S.slot_bytes);
     uint64_t* full = wbar + 1;
     uint64_t* empty = full + S.slots;
-    uint64_t* tfull = empty + S.slots;                   // [2]
-    uint64_t* tempty = tfull + 2;                        // [2]
-    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    uint64_t* tfull = empty + S.slots;                   // [nbuf]
+    uint64_t* tempty = tfull + S.nbuf;                   // [nbuf]
+    uint32_t* tslot = (uint32_t*)(tempty + S.nbuf);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gw = TCP_EPI_WARPS / S.groups;             // warps per epilogue group
 
     if (tid == 0) {
         mbar_init(wbar, 1);
@@ -498,16 +503,16 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < S.nbuf; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], TCP_EPI_WARPS);
+            mbar_init(&tempty[b], (uint32_t)gw);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(2 * S.ncols)
+                     "r"(S.nbuf * S.ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -545,8 +550,8 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
             const uint32_t wbase = smem_u32(wsm);
             int64_t it = 0;
             for (int64_t t = blockIdx.x; t < tiles && ok && !tc_failed(); t += gridDim.x, ++it) {
-                const int buf = (int)(it & 1);
-                const int64_t ubuf = it >> 1;
+                const int buf = (int)(it % S.nbuf);
+                const int64_t ubuf = it / S.nbuf;
                 if (ubuf > 0 && !mbar_wait(&tempty[buf], (uint32_t)((ubuf - 1) & 1))) break;
                 const int s = (int)(it % S.slots);
                 const int64_t use = it / S.slots;
@@ -568,19 +573,21 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
             }
         }
     } else {
-        int it = 0;
-        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
-            const int buf = it & 1, ubuf = it >> 1;
+        const int g = warp / gw, wi = warp - g * gw;
+        const int q = wi & 3;                            // lane quarter (warp % 4 == wi % 4)
+        for (int64_t it = g; blockIdx.x + it * gridDim.x < tiles; it += S.groups) {
+            const int64_t t = blockIdx.x + it * gridDim.x;
+            const int buf = (int)(it % S.nbuf);
+            const int64_t ubuf = it / S.nbuf;
             const bool have = mbar_wait(&tfull[buf], (uint32_t)(ubuf & 1));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!__all_sync(0xffffffffu, have && !tc_failed())) break;
             int64_t p0;
             int img, y0, x0;
             tile_origin(A, t, p0, img, y0, x0);
-            const int q = warp & 3;
             const int64_t p = p0 + q * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S.ncols);
-            for (int c = (warp >> 2) * 16; c < A.Cout; c += 16 * (TCP_EPI_WARPS / 4)) {
+            for (int c = (wi >> 2) * 16; c < A.Cout; c += 16 * (gw / 4)) {
                 uint32_t r[16];
                 tmem_ld16(trow + (uint32_t)c, r);
                 const int64_t o = p * A.CoutStride + c;
@@ -621,7 +628,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * S.ncols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S.nbuf * S.ncols)
                      : "memory");
     }
 }
@@ -750,6 +757,10 @@ static bool tch_shape(const ConvArgs& A, HaloShape& S, int& cps)
         if (sl > 6) sl = 6;
         if (sl >= 2) {
             S.slots = sl;
+            // two epilogue groups of four warps, each draining its own pair
+            // of accumulator buffers, where tensor memory holds four per CTA
+            S.groups = cps * 4 * nc <= 512 ? 2 : 1;
+            S.nbuf = 2 * S.groups;
             return true;
         }
     }
@@ -758,7 +769,8 @@ static bool tch_shape(const ConvArgs& A, HaloShape& S, int& cps)
 
 static size_t tch_smem(const HaloShape& S)
 {
-    return 1024 + (size_t)S.w_bytes + (size_t)S.slots * S.slot_bytes + (size_t)(1 + 2 * S.slots + 4) * 8 + 16;
+    return 1024 + (size_t)S.w_bytes + (size_t)S.slots * S.slot_bytes + (size_t)(1 + 2 * S.slots + 2 * S.nbuf) * 8 +
+           16;
 }
 
 static cudaError_t launch_tch(const ConvArgs& A, const HaloShape& S, int cps, cudaStream_t s)
