@@ -477,15 +477,130 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(UpdateArgs<T> A)
     }
 }
 
+// FP32 form with 16-byte accesses (rows and columns multiples of 4): a thread
+// owns row rr and four consecutive columns of the 32 x 32 tile, the
+// transposed block is staged four rows at a time; the arithmetic and its
+// order are those of update_kernel.
+template <int MODE, int R_>
+__global__ void __launch_bounds__(kUpdThreads) update_v4_kernel(UpdateArgs<float> A)
+{
+    __shared__ float sz[kTile][kTile + 1];
+    __shared__ float sx[kTile][kTile + 1];
+    const int64_t R = A.rows, W = A.cols;
+    const int64_t tiles_c = (W + kTile - 1) / kTile;
+    const int64_t r0 = (blockIdx.x / tiles_c) * kTile;
+    const int64_t c0 = (blockIdx.x % tiles_c) * kTile;
+    constexpr int last = R_ - 1;
+    const int q4 = threadIdx.x & 7, rr = threadIdx.x >> 3;          // 8 quads x 32 rows
+    {   // stage the transposed block: element (r0+i, c0+cc) at (c0+cc)*R + r0+i
+        const int cc = rr;
+        const int64_t c = c0 + cc, r = r0 + 4 * q4;
+        if (c < W && r < R) {
+            const float4 zv = *(const float4*)(A.s[last] + c * R + r);
+            const float4 xv = *(const float4*)(A.x[last] + c * R + r);
+            sz[cc][4 * q4 + 0] = zv.x; sz[cc][4 * q4 + 1] = zv.y; sz[cc][4 * q4 + 2] = zv.z; sz[cc][4 * q4 + 3] = zv.w;
+            sx[cc][4 * q4 + 0] = xv.x; sx[cc][4 * q4 + 1] = xv.y; sx[cc][4 * q4 + 2] = xv.z; sx[cc][4 * q4 + 3] = xv.w;
+        }
+    }
+    __syncthreads();
+    const int64_t r = r0 + rr, c = c0 + 4 * q4;
+    if (r < R && c < W) {
+        const int64_t g = r * W + c;
+        const float4 w4 = *(const float4*)(A.w + g);
+        float4 sv4[R_], xv4[R_];
+#pragma unroll
+        for (int k = 0; k < R_; ++k) {
+            if (k == last) {
+                sv4[k] = make_float4(sz[4 * q4 + 0][rr], sz[4 * q4 + 1][rr], sz[4 * q4 + 2][rr], sz[4 * q4 + 3][rr]);
+                xv4[k] = make_float4(sx[4 * q4 + 0][rr], sx[4 * q4 + 1][rr], sx[4 * q4 + 2][rr], sx[4 * q4 + 3][rr]);
+            } else {
+                sv4[k] = *(const float4*)(A.s[k] + g);
+                xv4[k] = *(const float4*)(A.x[k] + g);
+            }
+        }
+        float out[R_][4];
+        float xo[4];
+        const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float yk[R_];
+            float ysum = 0.f, ssum = 0.f;
+#pragma unroll
+            for (int k = 0; k < R_; ++k) {
+                const float sv = j == 0 ? sv4[k].x : j == 1 ? sv4[k].y : j == 2 ? sv4[k].z : sv4[k].w;
+                const float xv = j == 0 ? xv4[k].x : j == 1 ? xv4[k].y : j == 2 ? xv4[k].z : xv4[k].w;
+                yk[k] = sv - xv;
+                ysum += yk[k];
+                ssum += sv;
+            }
+            xo[j] = wv[j] - ysum;
+            float cc;
+            if constexpr (MODE == UPD_AAR) cc = (wv[j] - 2.f * ysum + ssum) / float(R_);
+            else cc = (wv[j] - ysum) / float(R_);
+#pragma unroll
+            for (int k = 0; k < R_; ++k) out[k][j] = yk[k] + cc;
+        }
+        if (A.check) *(float4*)(A.xout + g) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+        if constexpr (MODE != UPD_EVAL) {
+#pragma unroll
+            for (int k = 0; k < R_; ++k) {
+                if (k == last) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sz[4 * q4 + j][rr] = out[k][j];
+                } else {
+                    *(float4*)(A.s[k] + g) = make_float4(out[k][0], out[k][1], out[k][2], out[k][3]);
+                }
+            }
+        }
+    }
+    if constexpr (MODE != UPD_EVAL) {
+        __syncthreads();
+        const int cc = rr;
+        const int64_t c2 = c0 + cc, r2 = r0 + 4 * q4;
+        if (c2 < W && r2 < R)
+            *(float4*)(A.s[last] + c2 * R + r2) =
+                make_float4(sz[cc][4 * q4 + 0], sz[cc][4 * q4 + 1], sz[cc][4 * q4 + 2], sz[cc][4 * q4 + 3]);
+    }
+}
+
+template <typename T>
+static bool update_v4_ok(const UpdateArgs<T>& A)
+{
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        if (A.rows % 4 || A.cols % 4) return false;
+        uintptr_t m = (uintptr_t)A.w | (uintptr_t)A.xout;
+        for (int k = 0; k < A.r; ++k) m |= (uintptr_t)A.s[k] | (uintptr_t)A.x[k];
+        return (m & 15) == 0;
+    }
+}
+
 template <typename T>
 cudaError_t launch_update(int mode, const UpdateArgs<T>& A, cudaStream_t s)
 {
     const int64_t tiles = ((A.rows + kTile - 1) / kTile) * ((A.cols + kTile - 1) / kTile);
     if (tiles == 0) return cudaSuccess;
+    if (A.r != 2 && A.r != 3) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 4) {
+        if (update_v4_ok(A)) {
+            const UpdateArgs<float>& F = reinterpret_cast<const UpdateArgs<float>&>(A);
+#define TVCUT_UPD4(M)                                                                      \
+    (A.r == 3 ? (update_v4_kernel<M, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0)      \
+              : (update_v4_kernel<M, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0))
+            switch (mode) {
+            case UPD_AAR: TVCUT_UPD4(UPD_AAR); break;
+            case UPD_AP: TVCUT_UPD4(UPD_AP); break;
+            case UPD_EVAL: TVCUT_UPD4(UPD_EVAL); break;
+            default: return cudaErrorInvalidValue;
+            }
+#undef TVCUT_UPD4
+            return cudaGetLastError();
+        }
+    }
 #define TVCUT_UPD(M)                                                                       \
     (A.r == 3 ? (update_kernel<T, M, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A), 0)      \
               : (update_kernel<T, M, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(A), 0))
-    if (A.r != 2 && A.r != 3) return cudaErrorInvalidValue;
     switch (mode) {
     case UPD_AAR: TVCUT_UPD(UPD_AAR); break;
     case UPD_AP: TVCUT_UPD(UPD_AP); break;
