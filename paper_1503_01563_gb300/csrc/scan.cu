@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(UpdateArgs<T> A)
 // transposed block is staged four rows at a time; the arithmetic and its
 // order are those of update_kernel.
 template <int MODE, int R_>
-__global__ void __launch_bounds__(kUpdThreads) update_v4_kernel(UpdateArgs<float> A)
+__global__ void __launch_bounds__(kUpdThreads) update_kernel_v4(UpdateArgs<float> A)
 {
     __shared__ float sz[kTile][kTile + 1];
     __shared__ float sx[kTile][kTile + 1];
@@ -586,8 +586,8 @@ cudaError_t launch_update(int mode, const UpdateArgs<T>& A, cudaStream_t s)
         if (update_v4_ok(A)) {
             const UpdateArgs<float>& F = reinterpret_cast<const UpdateArgs<float>&>(A);
 #define TVCUT_UPD4(M)                                                                      \
-    (A.r == 3 ? (update_v4_kernel<M, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0)      \
-              : (update_v4_kernel<M, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0))
+    (A.r == 3 ? (update_kernel_v4<M, 3><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0)      \
+              : (update_kernel_v4<M, 2><<<(unsigned)tiles, kUpdThreads, 0, s>>>(F), 0))
             switch (mode) {
             case UPD_AAR: TVCUT_UPD4(UPD_AAR); break;
             case UPD_AP: TVCUT_UPD4(UPD_AP); break;
