@@ -371,6 +371,14 @@ tvcut_status tvcut_conv3x3_bf16_ex(const void* in, const void* wt, const float* 
  * error. */
 int tvcut_conv_tc_error(void);
 
+/* Test hook for the bounded waits: while on (nonzero), CTA 0 of every
+ * tcgen05 convolution launched skips its first operand load, so that its
+ * MMA issuer's wait gives up after 2 s; the launch then ends (every role of
+ * every CTA stops at its next tile and frees its tensor memory), its output
+ * is incomplete, and tvcut_conv_tc_error reports 1.  Off by default; the
+ * convolutions are unaffected while it is off. */
+tvcut_status tvcut_conv_tc_stall(int on);
+
 /* The U-Net's convolutions (forward and input gradient): engine 0 (default)
  * uses the persistent tcgen05 kernel for every layer whose shape it takes
  * and the mma.sync kernel for the others; 1 uses the mma.sync kernel

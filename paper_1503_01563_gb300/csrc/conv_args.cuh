@@ -28,6 +28,7 @@ bool conv_tc_supported(const ConvArgs& A);
 // without the halo form
 cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s, int form = 0);
 int conv_tc_take_error();
+int conv_tc_set_stall(int on);
 
 }  // namespace nn
 }  // namespace tvcut

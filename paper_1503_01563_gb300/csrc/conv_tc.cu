@@ -33,6 +33,9 @@ constexpr int TC_THREADS = 128;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 __device__ int g_conv_tc_error;
+// Test hook (tvcut_conv_tc_stall): while set, CTA 0 of every launch skips its
+// first operand load, so that its MMA issuer's bounded wait gives up.
+__device__ int g_conv_tc_stall;
 
 struct TcShape {
     int cblk;       // channels per K block (16, 32 or 64): one swizzle row
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const __grid_con
             const int ky = tap / 3, kx = tap - 3 * ky;
             uint8_t* sa = sm + (size_t)s * stage_bytes;
             mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+            if (kb == 0 && blockIdx.x == 0 && *(volatile int*)&g_conv_tc_stall) continue;
             tma_load_4d(sa, &tmA, c0, x0 + kx - 1, y0 + ky - 1, img, &full[s]);
             tma_load_3d(sa + S.a_bytes, &tmB, c0, 0, tap, &full[s]);
         }
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tcp_kernel(
                     const int ky = tap / 3, kx = tap - 3 * ky;
                     uint8_t* sa = sm + (size_t)s * stage_bytes;
                     mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+                    if (kbg == 0 && blockIdx.x == 0 && *(volatile int*)&g_conv_tc_stall) continue;
                     tma_load_4d(sa, &tmA, c0, x0 + kx - 1, y0 + ky - 1, img, &full[s]);
                     tma_load_3d(sa + S.a_bytes, &tmB, c0, 0, tap, &full[s]);
                 }
@@ -538,6 +543,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
                 tile_origin(A, t, p0, img, y0, x0);
                 uint8_t* slot = hsm + (size_t)s * S.slot_bytes;
                 mbar_expect_tx(&full[s], (uint32_t)(S.kch * 3 * HALO_W * 16));
+                if (it == 0 && blockIdx.x == 0 && *(volatile int*)&g_conv_tc_stall) continue;
                 for (int kc = 0; kc < S.kch; ++kc)
                     tma_load_4d(slot + (size_t)kc * S.kstride, &tmH, 8 * kc, x0 - 1, y0 - 1, img, &full[s]);
             }
@@ -877,6 +883,12 @@ cudaError_t launch_conv3x3_tc(const ConvArgs& A, cudaStream_t s, int form)
         conv3x3_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, s>>>(tmA, tmB, A, S);
     }
     return cudaGetLastError();
+}
+
+// Sets the stall test hook (see g_conv_tc_stall); < 0 on a CUDA error.
+int conv_tc_set_stall(int on)
+{
+    return cudaMemcpyToSymbol(g_conv_tc_stall, &on, sizeof(int)) == cudaSuccess ? 0 : -1;
 }
 
 // 1 if a tensor-core convolution gave up waiting since the last call (and

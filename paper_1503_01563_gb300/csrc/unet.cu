@@ -821,3 +821,9 @@ extern "C" int tvcut_conv_tc_error(void)
 {
     return conv_tc_take_error();
 }
+
+extern "C" tvcut_status tvcut_conv_tc_stall(int on)
+{
+    if (conv_tc_set_stall(on ? 1 : 0) != 0) return ufail(nullptr, TVCUT_ERR_CUDA, "tvcut_conv_tc_stall: cudaMemcpyToSymbol");
+    return TVCUT_OK;
+}

@@ -34,7 +34,7 @@ EXPORTED = [
     "tvcut_unet_create", "tvcut_unet_destroy", "tvcut_unet_last_error", "tvcut_unet_resize",
     "tvcut_unet_forward", "tvcut_unet_backward", "tvcut_unet_adam", "tvcut_unet_num_params",
     "tvcut_unet_get_params", "tvcut_unet_set_params", "tvcut_conv3x3_bf16", "tvcut_conv3x3_wgrad_bf16",
-    "tvcut_conv3x3_bf16_ex", "tvcut_conv_tc_error", "tvcut_unet_set_engine",
+    "tvcut_conv3x3_bf16_ex", "tvcut_conv_tc_error", "tvcut_unet_set_engine", "tvcut_conv_tc_stall",
 ]
 K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
         "tvcut_conv3x3_wgrad_bf16": (st, [P, P, P, c_int, c_int, c_int, c_int, c_int, P]),
         "tvcut_conv3x3_bf16_ex": (st, [P, P, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int, P]),
         "tvcut_conv_tc_error": (c_int, []),
+        "tvcut_conv_tc_stall": (st, [c_int]),
         "tvcut_unet_set_engine": (st, [P, c_int]),
     }
     for name, (res, args) in sig.items():

@@ -131,6 +131,40 @@ def test_conv_tcgen05_persistent_many_tiles(tv, shape):
     assert bool((d <= 2 ** -6 * torch.clamp(outs[2].abs(), min=1.0)).all())
 
 
+@pytest.mark.parametrize("engine,shape", [(2, (1, 16, 128, 16, 32)), (4, (1, 16, 128, 16, 32)),
+                                          (3, (1, 16, 128, 16, 32)), (2, (1, 8, 256, 64, 128))])
+def test_conv_tcgen05_bounded_wait_gives_up(tv, engine, shape):
+    """The stall hook makes CTA 0 skip its first operand load: the MMA
+    issuer's bounded wait gives up (2 s), the launch ends by itself, the
+    error flag reads 1 once and is cleared, and the context stays usable:
+    the next launch without the hook is complete and correct."""
+    n, h, w, ci, co = shape
+    g = torch.Generator(device="cuda").manual_seed(11)
+    xd = torch.randn((n, h, w, ci), generator=g, device="cuda").to(torch.bfloat16)
+    wd = (torch.randn((9, co, ci), generator=g, device="cuda") * 0.2).to(torch.bfloat16)
+    out = torch.zeros((n, h, w, co), dtype=torch.bfloat16, device="cuda")
+    ref = torch.zeros_like(out)
+    assert tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), None, ref.data_ptr(), n, h, w, ci, co, 0, 1,
+                                          None) == tv.OK
+    assert tv.lib().tvcut_conv_tc_error() == 0
+    try:
+        assert tv.lib().tvcut_conv_tc_stall(1) == tv.OK
+        assert tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), None, out.data_ptr(), n, h, w, ci, co, 0,
+                                              engine, None) == tv.OK
+        torch.cuda.synchronize()
+        assert tv.lib().tvcut_conv_tc_error() == 1
+        assert tv.lib().tvcut_conv_tc_error() == 0
+    finally:
+        assert tv.lib().tvcut_conv_tc_stall(0) == tv.OK
+    out.zero_()
+    assert tv.lib().tvcut_conv3x3_bf16_ex(xd.data_ptr(), wd.data_ptr(), None, out.data_ptr(), n, h, w, ci, co, 0,
+                                          engine, None) == tv.OK
+    torch.cuda.synchronize()
+    assert tv.lib().tvcut_conv_tc_error() == 0
+    d = (out.float() - ref.float()).abs()
+    assert bool((d <= 2 ** -6 * torch.clamp(ref.float().abs(), min=1.0)).all())
+
+
 def test_conv_tcgen05_rejects_other_shapes(tv):
     x = torch.zeros((2, 9, 13, 32), dtype=torch.bfloat16, device="cuda")
     wk = torch.zeros((9, 16, 32), dtype=torch.bfloat16, device="cuda")
