@@ -41,7 +41,7 @@ WORKLOADS = {
     "batch512": dict(grids=512, seed=4, cap=3000),
     # learned warm start: U-Net (4 levels, 32 channels) trained on solver-generated 128^2 problems,
     # evaluated on held-out 2048^2 problems (w ~ U{-50..50}, a ~ U{1..20}), cold vs warm
-    "warm2048": dict(dims=(2048, 2048), seed=999, cap=3000, train_n=4096, train_hw=128, train_steps=1500),
+    "warm2048": dict(dims=(2048, 2048), seed=999, cap=3000, train_n=4096, train_hw=128, train_steps=4000),
     # the warm-start network's inference alone: U-Net (4 levels, 32 channels) on one 2048^2 input,
     # randomly initialised weights; its 3x3 convolutions are the one dense contraction of the path
     "unet2048": dict(dims=(2048, 2048), seed=21, base=32),
