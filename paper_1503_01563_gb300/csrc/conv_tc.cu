@@ -151,7 +151,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+// Epilogue of one accumulator row (output pixel p, tensor-memory row trow)
+// for the 16-column chunks c0, c0 + cstep, ...: bias, ReLU, mask, BF16 (and
+// optional FP32) stores.  Every lane of the warp calls it (tcgen05.ld is
+// .sync.aligned).
+__device__ __forceinline__ void epilogue_row(const ConvArgs& A, int64_t p, uint32_t trow, int c0, int cstep)
+{
+    const bool vbias = A.bias && ((uintptr_t)A.bias & 15) == 0;
+    for (int c = c0; c < A.Cout; c += cstep) {
+        uint32_t r[16];
+        tmem_ld16(trow + (uint32_t)c, r);
+        const int64_t o = p * A.CoutStride + c;
+        __align__(16) __nv_bfloat16 ob[16];
+        __align__(16) __nv_bfloat16 mk[16];
+        __align__(16) float bs[16];
+        if (A.mask) {
+            *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
+            *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
+        }
+        if (vbias) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) *(float4*)&bs[j] = *(const float4*)(A.bias + c + j);
+        } else if (A.bias) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) bs[j] = A.bias[c + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float v = __uint_as_float(r[j]);
+            if (A.bias) v += bs[j];
+            if (A.relu) v = fmaxf(v, 0.f);
+            if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
+            ob[j] = __float2bfloat16(v);
+            if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
+        }
+        *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
+        *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 10) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ CUtensorMap tmB, ConvArgs A,
                                                                 TcShape S)
 {
@@ -231,33 +270,8 @@ __global__ void __launch_bounds__(TC_THREADS) conv3x3_tc_kernel(const __grid_con
     const bool have = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncwarp();
-    if (have && !*(volatile int*)&g_conv_tc_error) {
-        const int m = warp * 32 + lane;
-        const int64_t p = p0 + m;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < A.Cout; c += 16) {
-            uint32_t r[16];
-            tmem_ld16(trow + (uint32_t)c, r);
-            const int64_t o = p * A.CoutStride + c;
-            __align__(16) __nv_bfloat16 ob[16];
-            __align__(16) __nv_bfloat16 mk[16];
-            if (A.mask) {
-                *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
-                *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                float v = __uint_as_float(r[j]);
-                if (A.bias) v += A.bias[c + j];
-                if (A.relu) v = fmaxf(v, 0.f);
-                if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
-                ob[j] = __float2bfloat16(v);
-                if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
-            }
-            *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
-            *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
-        }
-    }
+    if (__all_sync(0xffffffffu, have && !*(volatile int*)&g_conv_tc_error))
+        epilogue_row(A, p0 + warp * 32 + lane, tmem + ((uint32_t)(warp * 32) << 16), 0, 16);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -404,38 +418,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tcp_kernel(
             const int m = q * 32 + lane;
             const int64_t p = p0 + m;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S.ncols);
-            for (int c = (warp >> 2) * 16; c < A.Cout; c += 16 * (TCP_EPI_WARPS / 4)) {
-                uint32_t r[16];
-                tmem_ld16(trow + (uint32_t)c, r);
-                const int64_t o = p * A.CoutStride + c;
-                __align__(16) __nv_bfloat16 ob[16];
-                __align__(16) __nv_bfloat16 mk[16];
-                __align__(16) float bs[16];
-                if (A.mask) {
-                    *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
-                    *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
-                }
-                if (A.bias) {
-                    if (((uintptr_t)A.bias & 15) == 0) {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 4) *(float4*)&bs[j] = *(const float4*)(A.bias + c + j);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) bs[j] = A.bias[c + j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float v = __uint_as_float(r[j]);
-                    if (A.bias) v += bs[j];
-                    if (A.relu) v = fmaxf(v, 0.f);
-                    if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
-                    ob[j] = __float2bfloat16(v);
-                    if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
-                }
-                *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
-                *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
-            }
+            epilogue_row(A, p, trow, (warp >> 2) * 16, 16 * (TCP_EPI_WARPS / 4));
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -593,38 +576,7 @@ __global__ void __launch_bounds__(TCP_THREADS, TCP_MAX_CTAS) conv3x3_tch_kernel(
             tile_origin(A, t, p0, img, y0, x0);
             const int64_t p = p0 + q * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S.ncols);
-            for (int c = (wi >> 2) * 16; c < A.Cout; c += 16 * (gw / 4)) {
-                uint32_t r[16];
-                tmem_ld16(trow + (uint32_t)c, r);
-                const int64_t o = p * A.CoutStride + c;
-                __align__(16) __nv_bfloat16 ob[16];
-                __align__(16) __nv_bfloat16 mk[16];
-                __align__(16) float bs[16];
-                if (A.mask) {
-                    *(uint4*)&mk[0] = *(const uint4*)(A.mask + o);
-                    *(uint4*)&mk[8] = *(const uint4*)(A.mask + o + 8);
-                }
-                if (A.bias) {
-                    if (((uintptr_t)A.bias & 15) == 0) {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 4) *(float4*)&bs[j] = *(const float4*)(A.bias + c + j);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) bs[j] = A.bias[c + j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float v = __uint_as_float(r[j]);
-                    if (A.bias) v += bs[j];
-                    if (A.relu) v = fmaxf(v, 0.f);
-                    if (A.mask && !(__bfloat162float(mk[j]) > 0.f)) v = 0.f;
-                    ob[j] = __float2bfloat16(v);
-                    if (A.out_f32) A.out_f32[p * A.Cout + c + j] = v;
-                }
-                *(uint4*)(A.out + o) = *(const uint4*)&ob[0];
-                *(uint4*)(A.out + o + 8) = *(const uint4*)&ob[8];
-            }
+            epilogue_row(A, p, trow, (wi >> 2) * 16, 16 * (gw / 4));
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
