@@ -12,12 +12,25 @@
 //      TMA box.
 //   D: FP32 accumulators in tensor memory (128 lanes x Cout columns).
 //
-// One thread issues the TMA loads into a ring of stages (mbarriers count the
-// bytes), one thread issues the MMAs and frees each stage with
-// tcgen05.commit; then all four warps read their 32 accumulator rows with
-// tcgen05.ld, add bias, apply ReLU / mask, and store BF16 (and FP32).  Every
-// wait is bounded by a 2 s clock; a wait that gives up raises an error flag
-// the host reads back, and the CTA still releases its tensor memory.
+// Three forms share these pieces:
+//   conv3x3_tc_kernel   one 128-pixel tile per CTA: one thread issues the TMA
+//                       loads into a ring of stages (mbarriers count the
+//                       bytes), one thread issues the MMAs and frees each
+//                       stage with tcgen05.commit; then all four warps read
+//                       their 32 accumulator rows with tcgen05.ld, add bias,
+//                       apply ReLU / mask, and store BF16 (and FP32);
+//   conv3x3_tcp_kernel  persistent CTAs with the producer, the MMA issuer and
+//                       eight epilogue warps in separate warps and two
+//                       tensor-memory accumulator buffers, so that one tile's
+//                       epilogue overlaps the next tiles' loads and MMAs;
+//   conv3x3_tch_kernel  the persistent form for 16-64 input channels with the
+//                       tile's three input rows loaded once per 8 channels
+//                       (the nine taps are descriptor offsets into them) and
+//                       the weights resident in shared memory.
+// The three issue the same MMAs in the same order, so their outputs are
+// identical.  Every wait is bounded by a 2 s clock; a wait that gives up
+// raises an error flag the host reads back, every role stops at its next
+// tile, and each CTA still releases its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
