@@ -5,22 +5,23 @@
 //   scan:   x_k = prox_{f_k}(s_k) on every chain of every block k at once.
 //           The blocks' projections are independent in the product space
 //           (Sec. 4.2: Pi_K splits into the Pi_{K_k}), so all axes share one
-//           launch; a thread, or a group of 4-32 lanes, owns one chain.  The
-//           prox is the taut string of Sec. 3.2 in local form (see
-//           scan_chain).  Each block's state is stored so that consecutive
-//           chains are consecutive in memory ("chain-major"): the natural
-//           row-major layout already is for every axis but the last, the last
-//           axis' block (rows) is kept transposed, and the zig-zag path
-//           blocks of an 8-connected grid use the transposed layout with rows
-//           swapped within pairs.  A warp's loads of one step are thus one
-//           128-byte line.
+//           launch; a thread (reading weights padded to the state layout, so
+//           that each element is loaded one step ahead), or a group of 4-32
+//           lanes, owns one chain.  The prox is the taut string of Sec. 3.2
+//           in local form (see scan_chain).  Each block's state is stored so
+//           that consecutive chains are consecutive in memory ("chain-major"):
+//           the natural row-major layout already is for every axis but the
+//           last, the last axis' block (rows) is kept transposed, and the
+//           zig-zag path blocks of an 8-connected grid use the transposed
+//           layout with rows swapped within pairs.  A warp's loads of one
+//           step are thus one 128-byte line.
 //
 //   update: per vertex, y_k = s_k - x_k and
 //             AAR (Eq. 3 with Eq. dualA): s_k <- y_k + (w - 2 sum y + sum s)/r
 //             AP  (Sec. 4.2):             s_k <- y_k + (w - sum y)/r
 //           and, on check iterations, the primal x = w - sum_k y_k (Sec. 2.3).
-//           Elementwise and coalesced; the transposed blocks go through
-//           shared-memory tiles.
+//           Elementwise and coalesced (16-byte accesses in FP32); the
+//           transposed blocks go through shared-memory tiles.
 //
 // BCD and FISTA (Sec. 4.1) hold the duals y_k; their passes form the point to
 // project (bcd_prepare_kernel, fista_prepare_kernel, prep8_kernel) and the
