@@ -449,7 +449,7 @@ struct tvcut_batch_ctx {
     // launch configuration (autotuned)
     int scan_threads = 128;
     int scan_ctas_per_sm = 8;
-    int scan_predicated = 1;          // step variant of the chain scan (VAR of batch_scan_kernel)
+    int scan_step = 1;                // form of the chain scan step (VAR of batch_scan_kernel)
     int sms = 152;
     // graph cache
     cudaGraphExec_t graph = nullptr;
@@ -834,7 +834,7 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
             batch_fista_kernel<T, false><<<b->sms * 16, 256, 0, b->stream>>>(A);
             e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
             if (e != cudaSuccess) return e;
-            if (b->scan_predicated == 1) batch_scan_kernel<T, 1, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            if (b->scan_step == 1) batch_scan_kernel<T, 1, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             else batch_scan_kernel<T, 0, true><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             batch_momentum_kernel<<<1, 1, 0, b->stream>>>(b->mom);
             std::swap(A.s0, A.p0);                // the new iterate is where the scan wrote
@@ -843,8 +843,8 @@ static cudaError_t enqueue(tvcut_batch_t b, int64_t iters)
         } else {
             e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
             if (e != cudaSuccess) return e;
-            if (b->scan_predicated == 2) batch_scan_kernel<T, 2, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
-            else if (b->scan_predicated == 1) batch_scan_kernel<T, 1, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            if (b->scan_step == 2) batch_scan_kernel<T, 2, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
+            else if (b->scan_step == 1) batch_scan_kernel<T, 1, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             else batch_scan_kernel<T, 0, false><<<scan_grid, b->scan_threads, 0, b->stream>>>(A);
             if (aar) batch_update_kernel<T, UPD_AAR><<<b->sms * 16, 256, 0, b->stream>>>(A);
             else batch_update_kernel<T, UPD_AP><<<b->sms * 16, 256, 0, b->stream>>>(A);
@@ -1038,7 +1038,7 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
     const int threads[] = {64, 128, 256};
     const int per_sm[] = {4, 8, 16};
     float best = 1e30f;
-    int bt = b->scan_threads, bp = b->scan_ctas_per_sm, bv = b->scan_predicated;
+    int bt = b->scan_threads, bp = b->scan_ctas_per_sm, bv = b->scan_step;
     for (int pv = 0; pv < 3; ++pv)
         for (int t : threads)
             for (int q : per_sm) {
@@ -1067,7 +1067,7 @@ static tvcut_status bautotune(tvcut_batch_t b, int* chosen)
     cudaEventDestroy(e1);
     b->scan_threads = bt;
     b->scan_ctas_per_sm = bp;
-    b->scan_predicated = bv;
+    b->scan_step = bv;
     if (chosen) {
         chosen[0] = bt;
         chosen[1] = bp;
@@ -1084,7 +1084,7 @@ extern "C" tvcut_status tvcut_batch_set_launch(tvcut_batch_t b, int threads, int
         return bfail(b, TVCUT_ERR_INVALID, "tvcut_batch_set_launch: threads 64/128/256, ctas_per_sm 1..32, step 0..2");
     b->scan_threads = threads;
     b->scan_ctas_per_sm = ctas_per_sm;
-    b->scan_predicated = step;
+    b->scan_step = step;
     drop_graph(b);
     return TVCUT_OK;
 }
