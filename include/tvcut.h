@@ -356,8 +356,12 @@ tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dout, float* d
  * (tensor memory accumulators, TMA-loaded operands; persistent CTAs with
  * the TMA producer, the MMA issuer and the epilogue in separate warps and
  * two accumulator buffers, so that one tile's epilogue overlaps the next
- * tile's loads and MMAs), 3 the tcgen05 kernel with one 128-pixel tile per
- * CTA.  2 and 3 are INVALID for shapes the tcgen05 kernel does not take: it
+ * tile's loads and MMAs; for 16-64 input channels the tile's three input
+ * rows are loaded once and all nine taps read from them), 3 the tcgen05
+ * kernel with one 128-pixel tile per CTA, 4 the persistent tcgen05 kernel
+ * without the three-row form.  All tcgen05 forms issue the same MMAs in the
+ * same order, so their outputs are identical.  2-4 are INVALID for shapes
+ * the tcgen05 kernel does not take: it
  * needs Cin 16, 32 or a multiple of 64, Cout <= 256, W a multiple of 128 or
  * a divisor of 128, H*W a multiple of 128, 16-byte aligned tensors.
  * Stream-ordered; a tcgen05 launch that gives up waiting (2 s per wait) is
@@ -382,7 +386,8 @@ tvcut_status tvcut_conv_tc_stall(int on);
 /* The U-Net's convolutions (forward and input gradient): engine 0 (default)
  * uses the persistent tcgen05 kernel for every layer whose shape it takes
  * and the mma.sync kernel for the others; 1 uses the mma.sync kernel
- * throughout; 3 is 0 with the one-tile-per-CTA tcgen05 kernel. */
+ * throughout; 3 is 0 with the one-tile-per-CTA tcgen05 kernel, 4 is 0
+ * without the three-row form (the engines of tvcut_conv3x3_bf16_ex). */
 tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine);
 
 /* Iterations without any device allocation.  The paper has no counterpart:
