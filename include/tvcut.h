@@ -395,13 +395,19 @@ tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine);
  * device memory -- code whose framework allocator owns all of the GPU's
  * memory, or latency-critical loops where a cudaMalloc (which can
  * synchronise the device) is not acceptable.  It runs `iters` iterations of
- * `algo` (TVCUT_AAR or TVCUT_AP) exactly like tvcut_iterate, on caller-owned
- * DEVICE buffers of element type `dtype` (TVCUT_F32 or TVCUT_F64):
+ * `algo` (TVCUT_AAR or TVCUT_AP), the same iteration as tvcut_iterate, on
+ * caller-owned DEVICE buffers of element type `dtype` (TVCUT_F32 or
+ * TVCUT_F64).  It always takes the fused per-block sweep kernels (one launch
+ * per block and iteration), not the all-blocks scan plus separate update that
+ * tvcut_iterate uses on large grids, so the two agree within rounding (FP64
+ * 1e-9, FP32 1e-4 of max|x| in the tests), not bit for bit, and this path is
+ * the slower of the two.  Buffers:
  *   w      n unary values;
  *   a      a[k] = axis k's compact edge weights (k < ndim);
  *   state  ndim*n product-space state (z for AAR, lambda for AP), updated in
  *          place -- start from zeros (AAR) or w/ndim in every block (AP);
- *   x      NULL, or n values that receive the primal of the last iteration.
+ *   x      NULL, or n values that receive the primal of the last iteration
+ *          (left unwritten when iters == 0).
  * The one scratch array an iteration needs (a per-vertex running sum) is a
  * fixed 8 MiB array inside the library image, so grids are limited to
  * 2^21 vertices with TVCUT_F32 and 2^20 with TVCUT_F64; larger grids return

@@ -287,19 +287,66 @@ def tvcut_profile_read(h):
     return ms, n
 
 
+def _noalloc_check(dims, w, a, state, x):
+    """Shape and dtype checks of tvcut_iterate_noalloc's buffers, made before
+    any pointer reaches the library: the C side trusts the sizes it derives
+    from ``dims``, so a short or mistyped buffer would be read or written past
+    its end on the device."""
+    dims = tuple(int(d) for d in dims)
+    if len(dims) not in (2, 3):
+        raise ValueError("dims must have 2 or 3 entries")
+
+    def meta(t, name):
+        if t is None:
+            raise ValueError(f"{name} is required")
+        return tuple(int(d) for d in t.shape), str(t.dtype)
+
+    wshape, wdt = meta(w, "w")
+    if wshape != dims:
+        raise ValueError(f"w must have shape {dims}, got {wshape}")
+    if not (wdt.endswith("float32") or wdt.endswith("float64")):
+        raise ValueError(f"w must be float32 or float64, got {wdt}")
+    if len(a) != len(dims):
+        raise ValueError(f"need {len(dims)} weight arrays (one per axis), got {len(a)}")
+    for k, ak in enumerate(a):
+        want = tuple(d - 1 if j == k else d for j, d in enumerate(dims))
+        shp, dt = meta(ak, f"a[{k}]")
+        if shp != want:
+            raise ValueError(f"a[{k}] must have shape {want}, got {shp}")
+        if dt != wdt:
+            raise ValueError(f"a[{k}] has dtype {dt}; every buffer must have w's dtype {wdt}")
+    shp, dt = meta(state, "state")
+    if shp != (len(dims),) + dims:
+        raise ValueError(f"state must have shape {(len(dims),) + dims}, got {shp}")
+    if dt != wdt:
+        raise ValueError(f"state has dtype {dt}; every buffer must have w's dtype {wdt}")
+    if x is not None:
+        shp, dt = meta(x, "x")
+        if shp != dims:
+            raise ValueError(f"x must have shape {dims}, got {shp}")
+        if dt != wdt:
+            raise ValueError(f"x has dtype {dt}; every buffer must have w's dtype {wdt}")
+    return dims
+
+
 def tvcut_iterate_noalloc(dims, algo, w, a, state, x=None, iters=1, stream=None):
     """Iterations on caller-owned device tensors, with no device allocation
-    inside the library (see include/tvcut.h).  w, a[k], state, x: CUDA
-    tensors of one float dtype; state has shape (ndim,) + dims."""
-    dims_arr = (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+    inside the library (see include/tvcut.h).  w, a[k], state, x: contiguous
+    CUDA tensors of one float dtype; a[k] has the grid's shape with dims[k]-1
+    along axis k; state has shape (ndim,) + dims.  With iters == 0 nothing
+    runs and x is left as it is."""
+    dims = _noalloc_check(dims, w, a, state, x)
+    dims_arr = (ctypes.c_int64 * len(dims))(*dims)
     pw, sw, dt, _ = _buf(w)
     bufs = [_buf(ak) for ak in a]
     ps, ss, dts, _ = _buf(state)
-    px = _buf(x)[0] if x is not None else None
-    if sw != DEVICE or ss != DEVICE or any(b[1] != DEVICE for b in bufs):
+    xb = _buf(x) if x is not None else None
+    if (sw != DEVICE or ss != DEVICE or any(b[1] != DEVICE for b in bufs)
+            or (xb is not None and xb[1] != DEVICE)):
         raise ValueError("tvcut_iterate_noalloc takes device tensors")
     arr = (ctypes.c_void_p * len(bufs))(*[b[0].value for b in bufs])
     s = ctypes.c_void_p(int(stream) if stream else 0)
+    px = xb[0] if xb is not None else None
     return _check(lib().tvcut_iterate_noalloc(len(dims), dims_arr, int(algo), dt, pw, arr, ps, px, int(iters), s))
 
 

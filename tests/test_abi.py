@@ -65,3 +65,42 @@ def test_no_oracle_in_product_path():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "oracle.h" not in src and "liboracle" not in src, f
+
+
+def _noalloc_args(dims=(6, 5), dt="float32"):
+    import numpy as np
+    w = np.zeros(dims, dt)
+    a = [np.zeros(tuple(d - 1 if j == k else d for j, d in enumerate(dims)), dt) for k in range(len(dims))]
+    state = np.zeros((len(dims),) + dims, dt)
+    x = np.zeros(dims, dt)
+    return dims, w, a, state, x
+
+
+@pytest.mark.parametrize("case", ["state_dtype", "a_dtype", "x_dtype", "state_shape", "w_shape", "a_shape",
+                                  "a_count", "x_shape", "host_buffers"])
+def test_noalloc_wrapper_rejects_mismatched_buffers(case):
+    """tvcut_iterate_noalloc's binding checks every buffer's dtype and shape
+    before a pointer reaches the library (no GPU needed: nothing is called)."""
+    import numpy as np
+    from paper_1503_01563_gb300 import tvcut
+    dims, w, a, state, x = _noalloc_args()
+    if case == "state_dtype":
+        state = state.astype(np.float64)
+    elif case == "a_dtype":
+        a[1] = a[1].astype(np.float64)
+    elif case == "x_dtype":
+        x = x.astype(np.float64)
+    elif case == "state_shape":
+        state = state[:1]
+    elif case == "w_shape":
+        w = w[:-1]
+    elif case == "a_shape":
+        a[0] = np.zeros(dims, np.float32)
+    elif case == "a_count":
+        a = a[:1]
+    elif case == "x_shape":
+        x = x.ravel()
+    with pytest.raises(ValueError) as e:
+        tvcut.tvcut_iterate_noalloc(dims, tvcut.AAR, w, a, state, x, 1)
+    if case == "host_buffers":
+        assert "device tensors" in str(e.value)

@@ -2,9 +2,10 @@
 allocate device memory (a framework allocator that owns the GPU's memory, or
 a latency-critical loop where a cudaMalloc is not acceptable).  Its only
 scratch is a fixed array inside the library image; this checks that its
-results match the handle-based entry point (tvcut_iterate) within the FP32
-tolerance used by the other GPU tests (1e-4 of max|x|), on two calls in a
-row that share that array, and that oversized grids are refused."""
+results match the CPU oracle's iterations (FP64) and the handle-based entry
+point (tvcut_iterate) within the tolerance used by the other GPU tests
+(FP32 1e-4, FP64 1e-9 of max|x|), on two calls in a row that share that
+array, and that oversized grids are refused."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,7 @@ def rel_err(got, want):
 
 @pytest.mark.parametrize("algo", [0, 1])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_noalloc_matches_handle_two_calls(tv, algo, dtype):
+def test_noalloc_matches_oracle_and_handle_two_calls(tv, orc, algo, dtype):
     tdt = torch.float32 if dtype == "f32" else torch.float64
     code = tv.F32 if dtype == "f32" else tv.F64
     tol = 1e-4 if dtype == "f32" else 1e-9
@@ -46,6 +47,7 @@ def test_noalloc_matches_handle_two_calls(tv, algo, dtype):
     for call, (w, a) in enumerate(problems):          # two calls in a row share the scratch
         iters = 13 + call
         want_state, want_x = via_handle(tv, w, a, algo, code, iters)
+        ref_state, ref_x = orc.iterate(algo, w, a, orc.cold_state(algo, w), iters)
         r = w.ndim
         wd = torch.from_numpy(w).to("cuda", tdt)
         ad = [torch.from_numpy(x).to("cuda", tdt) for x in a]
@@ -56,8 +58,11 @@ def test_noalloc_matches_handle_two_calls(tv, algo, dtype):
         x = torch.empty_like(wd)
         tv.tvcut_iterate_noalloc(w.shape, algo, wd, ad, state, x, iters)
         torch.cuda.synchronize()
-        assert rel_err(state.cpu().numpy(), want_state) < tol, call
-        assert rel_err(x.cpu().numpy(), want_x) < tol, call
+        got_state, got_x = state.cpu().numpy(), x.cpu().numpy()
+        assert rel_err(got_state, ref_state) < tol, call
+        assert rel_err(got_x, ref_x) < tol, call
+        assert rel_err(got_state, want_state) < tol, call
+        assert rel_err(got_x, want_x) < tol, call
 
 
 def test_noalloc_rejects_oversized_grid(tv):
