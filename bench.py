@@ -191,33 +191,64 @@ class ClockSampler:
 ALGOS = {"aar": 0, "ap": 1, "bcd": 2, "fista": 3}
 
 
-def cpu_leg(name, w, a, budget_s=12.0, algo="aar"):
-    """Oracle (FP64, the same algorithm, its taut-string prox with OpenMP over
-    chains) on the host cores, timed on a bounded sample: whole-grid
-    iterations until the time budget is spent; plus the oracle's exact
-    min-cut value E*."""
+def oracle_module(a):
     import oracle
     oracle.build()
-    orc = oracle
     if len(a) == 4:                    # 8-connected 2D grid
-        from oracle import conn8 as orc
-    cores = os.cpu_count() or 1
+        from oracle import conn8
+        return conn8
+    return oracle
+
+
+def exact_min_cut(w, a):
+    """The oracle's exact min-cut value E* (push-relabel max-flow) and its time."""
+    orc = oracle_module(a)
     t0 = time.perf_counter()
     e_star = orc.maxflow(w, a, 1)[1]
-    t_mf = time.perf_counter() - t0
+    return e_star, time.perf_counter() - t0
+
+
+def cpu_leg(name, w, a, kstar, budget_s=12.0, algo="aar", t_mf=0.0):
+    """The oracle (FP64, the same algorithm, its taut-string prox with OpenMP
+    over chains) on the host cores.  With k* known it runs exactly k*
+    iterations from the cold start, keeping the primal at k*/2 and k* for the
+    FP32-vs-FP64 comparison, and is timed over them; otherwise whole-grid
+    iterations until the time budget is spent."""
+    orc = oracle_module(a)
+    cores = os.cpu_count() or 1
     n = int(np.prod(w.shape))
     code = ALGOS[algo]
     s = orc.cold_state(code, w)
-    iters, t_it = 0, 0.0
-    while t_it < budget_s and iters < 200:
-        t0 = time.perf_counter()
-        s, _ = orc.iterate(code, w, a, s, 1, nthreads=cores)
-        t_it += time.perf_counter() - t0
-        iters += 1
+    xs = {}
+    t_it, iters = 0.0, 0
+    if kstar:
+        marks = sorted(set([max(1, kstar // 2), kstar]))
+        if algo == "fista":            # the oracle's FISTA momentum restarts per call: one call per mark
+            for k in marks:
+                t0 = time.perf_counter()
+                _, xs[k] = orc.iterate(code, w, a, orc.cold_state(code, w), k, nthreads=cores)
+                dt = time.perf_counter() - t0
+                if k == kstar:
+                    t_it, iters = dt, k
+        else:
+            done = 0
+            for k in marks:
+                t0 = time.perf_counter()
+                s, xs[k] = orc.iterate(code, w, a, s, k - done, nthreads=cores)
+                t_it += time.perf_counter() - t0
+                done = k
+            iters = kstar
+        sample = f"{iters} FP64 {algo.upper()} iterations (k*) over the full {name} grid ({t_it:.1f} s)"
+    else:
+        while t_it < budget_s and iters < 200:
+            t0 = time.perf_counter()
+            s, _ = orc.iterate(code, w, a, s, 1, nthreads=cores)
+            t_it += time.perf_counter() - t0
+            iters += 1
+        sample = f"{iters} FP64 {algo.upper()} iterations over the full {name} grid ({t_it:.1f} s)"
     value = n * iters / t_it / 1e6
-    return e_star, {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                    "sample": f"{iters} FP64 {algo.upper()} iterations over the full {name} grid ({t_it:.1f} s), "
-                              f"OpenMP over chains; max-flow E* took {t_mf:.1f} s"}
+    return xs, {"value": value, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
+                "sample": sample + f", OpenMP over chains; max-flow E* took {t_mf:.1f} s"}
 
 
 def run_reference(args):
@@ -461,17 +492,15 @@ def run_batch(args):
     return 0
 
 
-def run_warm(args):
-    """Cold-started iteration (AAR by default, --algo) vs the same iteration
-    started from the U-Net's predicted block duals (the AAR/AP state z = y_hat,
-    the BCD/FISTA state y = y_hat), both to the oracle-equal cut, on one GPU."""
+def warm_vs_cold(args, algos, local=0, cpu_leg=True):
+    """Cold-started iteration vs the same iteration started from the U-Net's
+    predicted block duals (AAR/AP state z = y_hat, BCD/FISTA state y = y_hat),
+    both to the oracle-equal cut, on the 2048^2 warm-start problem, for each
+    of `algos`.  The network is trained first (untimed); each timed warm step
+    includes the prediction (device features, forward pass, rescaling into
+    the state: tvcut_unet_predict_state).  Clocks are sampled over the timed
+    region."""
     import torch
-
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if rank != 0:
-        return 0                                   # single-GPU workload: extra ranks idle
-    torch.cuda.set_device(local)
     from paper_1503_01563_gb300 import learn, tvcut
     wl = WORKLOADS["warm2048"]
     dims = wl["dims"]
@@ -482,15 +511,17 @@ def run_warm(args):
     t0 = time.perf_counter()
     e_star = oracle.maxflow(w, a, 1)[1]
     t_mf = time.perf_counter() - t0
-    cores = os.cpu_count() or 1
-    algo = ALGOS[args.algo]
-    st0 = oracle.cold_state(algo, w)
-    t0 = time.perf_counter()
-    oracle.iterate(algo, w, a, st0, 2, nthreads=cores)
-    t_it = time.perf_counter() - t0
-    cpu_base = {"value": 2 * n / t_it / 1e6, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
-                "sample": f"2 FP64 {args.algo.upper()} iterations over the 2048^2 grid ({t_it:.1f} s); "
-                          f"max-flow E* {t_mf:.1f} s"}
+    cpu_base = None
+    if cpu_leg:
+        cores = os.cpu_count() or 1
+        code0 = ALGOS[algos[0]]
+        st0 = oracle.cold_state(code0, w)
+        t0 = time.perf_counter()
+        oracle.iterate(code0, w, a, st0, 2, nthreads=cores)
+        t_it = time.perf_counter() - t0
+        cpu_base = {"value": 2 * n / t_it / 1e6, "unit": "Mvertex-iter/s", "cores": cores, "kind": "oracle",
+                    "sample": f"2 FP64 {algos[0].upper()} iterations over the 2048^2 grid ({t_it:.1f} s); "
+                              f"max-flow E* {t_mf:.1f} s"}
     stream = torch.cuda.current_stream()
     # training (untimed): solver-generated targets, GPU forward/backward/Adam
     t0 = time.perf_counter()
@@ -502,65 +533,101 @@ def run_warm(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, Y
-    s = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
-    s.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
+    wd = torch.from_numpy(w).cuda()
+    ad = [torch.from_numpy(x).cuda() for x in a]
+    res = {"workload": "warm2048", "dims": list(dims), "oracle_min_cut": e_star, "iterate": "f32",
+           "network": "U-Net 4 levels, 32 channels, BF16 weights/activations, FP32 accumulation",
+           "training": f"{wl['train_n']} solver-generated {wl['train_hw']}^2 problems, {wl['train_steps']} Adam "
+                       f"steps of 16 (data {t_data:.1f} s, training {t_train:.1f} s, loss {hist[0]:.4f} -> "
+                       f"{float(np.mean(hist[-20:])):.4f})",
+           "step": "cold: cold start + k_cold iterations; warm: tvcut_unet_predict_state + k_warm iterations; "
+                   "both end at the oracle-equal cut",
+           "l2": "256 MB buffer written before each timed solve"}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for name in algos:
+        algo = ALGOS[name]
+        s = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream)
+        s.set_problem(wd, ad)
 
-    def probe(z0):
-        if z0 is None:
-            s.reset()
-        else:
-            tvcut.tvcut_set_state(s.h, z0)
-        for k in range(1, wl["cap"] + 1):
-            _, st = s.iterate(1)
-            if st.energy_i64 == e_star:
-                return k
-        return None
-    k_cold = probe(None)
-    z0 = learn.predict_state(net, w, a)
-    k_warm = probe(z0)
-    timed = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream)
-    timed.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
-    feats = torch.from_numpy(learn.features(w, a)[0][None]).cuda()
-    sc = learn.features(w, a)[1]
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    cold_ms, warm_ms, inf_ms, ok = [], [], [], True
-    for rep in range(args.warmup + args.steps):
-        ev[0].record(stream)
-        timed.reset()
-        _, st = timed.iterate(k_cold or wl["cap"])
-        ev[1].record(stream)
-        ok = ok and st.energy_i64 == e_star
-        out = net.forward(feats)
-        zw = (out[0].permute(2, 0, 1) * sc).contiguous()
-        ev[2].record(stream)
-        tvcut.tvcut_set_state(timed.h, zw)
-        _, st = timed.iterate(k_warm or wl["cap"])
-        ev[3].record(stream)
-        ev[3].synchronize()
-        ok = ok and st.energy_i64 == e_star
-        if rep >= args.warmup:
-            cold_ms.append(ev[0].elapsed_time(ev[1]))
-            inf_ms.append(ev[1].elapsed_time(ev[2]))
-            warm_ms.append(ev[1].elapsed_time(ev[3]))
-    cold = float(np.median(cold_ms))
-    warm = float(np.median(warm_ms))
-    out = {"metric": "Mvertex-iter/s", "value": n * (k_cold or wl["cap"]) / (cold / 1e3) / 1e6,
-           "unit": "Mvertex-iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": cold,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "warm2048", "dims": list(dims), "algo": args.algo.upper(), "iterate": "f32",
-                      "network": "U-Net 4 levels, 32 channels, BF16 weights/activations, FP32 accumulation",
-                      "training": f"{wl['train_n']} solver-generated {wl['train_hw']}^2 problems, "
-                                  f"{wl['train_steps']} Adam steps of 16 (data {t_data:.1f} s, training {t_train:.1f} s, "
-                                  f"loss {hist[0]:.4f} -> {float(np.mean(hist[-20:])):.4f})"},
-           "time_to_oracle_equal_cut_ms": {"cold": cold if k_cold else None, "warm": warm if k_warm else None,
-                                           "warm_inference": float(np.median(inf_ms))},
-           "iters_to_oracle_equal_cut": {"cold": k_cold, "warm": k_warm}, "oracle_min_cut": e_star,
-           "step_energies_match": ok, "cpu_baseline": cpu_base,
-           "roofline": None, "e2e": None, "clocks": None, "gpu_launches": None}
-    print(json.dumps(out), flush=True)
-    s.close()
-    timed.close()
+        def probe(warm):
+            if warm:
+                net.predict_state(s)
+            else:
+                s.reset()
+            for k in range(1, wl["cap"] + 1):
+                _, st = s.iterate(1)
+                if st.energy_i64 == e_star:
+                    return k
+            return None
+        k_cold = probe(False)
+        k_warm = probe(True)
+        s.close()
+        timed = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream)
+        timed.set_problem(wd, ad)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        cold_ms, warm_ms, inf_ms, ok = [], [], [], True
+        clocks = ClockSampler(local)
+        for rep in range(args.warmup + args.steps):
+            if rep == args.warmup:
+                torch.cuda.synchronize()
+                clocks.start()
+            flush.zero_()
+            ev[0].record(stream)
+            timed.reset()
+            _, st = timed.iterate(k_cold or wl["cap"])
+            ev[1].record(stream)
+            ok = ok and st.energy_i64 == e_star
+            flush.zero_()
+            ev[2].record(stream)
+            net.predict_state(timed)
+            ev[3].record(stream)
+            _, st = timed.iterate(k_warm or wl["cap"])
+            ev[4].record(stream)
+            ev[4].synchronize()
+            ok = ok and st.energy_i64 == e_star
+            if rep >= args.warmup:
+                cold_ms.append(ev[0].elapsed_time(ev[1]))
+                inf_ms.append(ev[2].elapsed_time(ev[3]))
+                warm_ms.append(ev[2].elapsed_time(ev[4]))
+        clk = clocks.stop()
+        timed.close()
+        cold, warm = float(np.median(cold_ms)), float(np.median(warm_ms))
+        res[name] = {"iters": {"cold": k_cold, "warm": k_warm},
+                     "ms": {"cold": cold if k_cold else None, "warm": warm if k_warm else None,
+                            "warm_prediction": float(np.median(inf_ms))},
+                     "warm_faster": bool(k_cold and k_warm and warm < cold),
+                     "cold_Mvertex_iter_s": n * (k_cold or wl["cap"]) / (cold / 1e3) / 1e6,
+                     "energies_match": ok, "clocks": clk}
     net.close()
+    return res, cpu_base
+
+
+def run_warm(args):
+    """The warm2048 workload on its own line (--algo picks the iteration)."""
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank != 0:
+        return 0                                   # single-GPU workload: extra ranks idle
+    torch.cuda.set_device(local)
+    res, cpu_base = warm_vs_cold(args, [args.algo], local)
+    r = res[args.algo]
+    n = int(np.prod(res["dims"]))
+    cold = r["ms"]["cold"]
+    out = {"metric": "Mvertex-iter/s", "value": r["cold_Mvertex_iter_s"], "unit": "Mvertex-iter/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": cold, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "warm2048", "dims": res["dims"], "algo": args.algo.upper(), "iterate": "f32",
+                      "network": res["network"], "training": res["training"], "step": res["step"],
+                      "l2": res["l2"]},
+           "time_to_oracle_equal_cut_ms": {"cold": cold, "warm": r["ms"]["warm"],
+                                           "warm_prediction": r["ms"]["warm_prediction"]},
+           "iters_to_oracle_equal_cut": r["iters"], "oracle_min_cut": res["oracle_min_cut"],
+           "step_energies_match": r["energies_match"], "cpu_baseline": cpu_base,
+           "roofline": None, "e2e": None, "clocks": r["clocks"], "gpu_launches": None,
+           "vertices": n}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -687,10 +754,10 @@ def run_ours(args):
     ndim = 4 if conn == 8 else len(dims)          # blocks per iteration
     algo = ALGOS[args.algo]
 
-    # CPU leg (rank 0): oracle E* and the oracle's own throughput
-    e_star, cpu_base = None, None
+    # the oracle's exact min-cut value E* (rank 0)
+    e_star, t_mf = (None, 0.0)
     if rank == 0:
-        e_star, cpu_base = cpu_leg(args.workload, w, a, budget_s=args.cpu_budget, algo=args.algo)
+        e_star, t_mf = exact_min_cut(w, a)
 
     stream = torch.cuda.current_stream(dev)
     wd = torch.from_numpy(w).to(dev)
@@ -710,6 +777,25 @@ def run_ours(args):
                 break
         probe.close()
     iters = kstar if kstar else cap
+
+    # CPU leg (rank 0): the oracle to k*, timed, and the FP32 primal against its FP64 one at k*/2 and k*
+    cpu_base, drift = None, None
+    if rank == 0:
+        xs, cpu_base = cpu_leg(args.workload, w, a, kstar, budget_s=args.cpu_budget, algo=args.algo, t_mf=t_mf)
+        if xs:
+            chk = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream,
+                               connectivity=conn)
+            chk.set_problem(wd, ad)
+            drift, done = {}, 0
+            for k in sorted(xs):
+                chk.iterate(k - done)
+                done = k
+                ref = xs[k]
+                got = chk.primal()
+                drift[str(k)] = float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30))
+            chk.close()
+            drift = {"max_abs_rel_primal": drift, "reference": "FP64 oracle, same iterations from the cold start",
+                     "tolerance": 1e-4}
     if world > 1:
         t = torch.tensor([iters], device=dev)
         dist.broadcast(t, 0)
@@ -797,6 +883,44 @@ def run_ours(args):
             e2e_s += time.perf_counter() - t0
     e2e_value = world * n * iters * e2e_steps / e2e_s / 1e6
 
+    # the library's own stop rules (no oracle k*): `certified` (energy - the rigorous bound < 1: a proof)
+    # and, for FP32 iterates, stop_on_approx (energy - the iterate's own bound < 1: not a proof); FP64
+    # iterates beside them for the rigorous rule
+    own = None
+    if rank == 0:
+        own = {"rules": {"certified": "energy - certified_lb < 1 (Sec. 2.2 bound from exactly feasible block "
+                                      "duals, FP64): a proof of optimality",
+                         "approx": "stop_on_approx: energy - discrete_lb < 1 with the iterate's own dual: not a "
+                                   "proof"}, "cap": cap}
+        for tag, dtype, approx_rule, everies in (("f32_approx", tvcut.F32, 1, (5, 10)),
+                                                 ("f32_certified", tvcut.F32, 0, (10,)),
+                                                 ("f64_certified", tvcut.F64, 0, (5, 10))):
+            for every in everies:
+                sv = tvcut.Solver(dims, algo=algo, dtype=dtype, check_every=every, stream=stream.cuda_stream,
+                                  connectivity=conn, stop_on_approx=approx_rule,
+                                  certify=1 if tag == "f32_certified" else 0)
+                sv.set_problem(wd, ad)
+                times, res = [], None
+                for rep in range(1 if tag == "f32_certified" else 3):
+                    flush.zero_()
+                    ev0.record(stream)
+                    tvcut.tvcut_reset(sv.h)
+                    code, st = sv.iterate(cap if tag != "f32_certified" else min(cap, 300))
+                    ev1.record(stream)
+                    ev1.synchronize()
+                    times.append(ev0.elapsed_time(ev1))
+                    res = (code, st)
+                code, st = res
+                own[f"{tag}_check_every_{every}"] = {
+                    "ms": float(np.median(times)), "iters": int(st.iters), "stopped": bool(code == tvcut.OK),
+                    "certified": bool(st.certified), "energy_equals_oracle": bool(st.energy_i64 == e_star),
+                    "energy_minus_certified_lb": (float(st.energy_i64 - st.certified_lb)
+                                                  if np.isfinite(st.certified_lb) else None)}
+                sv.close()
+    warm = None
+    if rank == 0 and args.workload == "volume256" and args.algo == "aar" and not args.no_warm:
+        warm, _ = warm_vs_cold(args, ["aar", "bcd"], local, cpu_leg=False)
+
     out = None
     if rank == 0:
         out = {
@@ -809,8 +933,14 @@ def run_ours(args):
                        "iters_per_step": iters, "step": "cold start + iterations to the oracle-equal cut + cut",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB buffer written between steps"},
-            "time_to_oracle_equal_cut_ms": {"cold": ms_per_step if kstar else None, "warm": None},
+            "time_to_oracle_equal_cut_ms": {
+                "cold": ms_per_step if kstar else None, "warm": None,
+                "warm2048": None if warm is None else {
+                    k: warm[k]["ms"] for k in ("aar", "bcd")}},
             "iters_to_oracle_equal_cut": kstar, "oracle_min_cut": e_star,
+            "time_to_cut_own_stop_ms": own,
+            "fp32_vs_fp64": drift,
+            "warm_start_2048": warm,
             "step_energies_match": all(e == e_star for e in energies),
             "roofline": roofline, "cpu_baseline": cpu_base,
             "e2e": {"value": e2e_value, "unit": "Mvertex-iter/s", "h2d_bytes_per_step": h2d,
@@ -836,6 +966,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="volume256")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-warm", action="store_true",
+                    help="skip the 2048^2 warm-vs-cold pair that the default volume256 line carries")
     ap.add_argument("--unet-hw", type=int, default=2048,
                     help="image size of the unet2048 workload (a multiple of 128; smaller for profiling)")
     ap.add_argument("--algo", choices=sorted(ALGOS), default="aar",

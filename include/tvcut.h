@@ -116,7 +116,19 @@ typedef struct {
                             (r, c+1)-(r+1, c), both (H-1) x (W-1) row-major.
                             8 needs ndim 2 and the scan schedule (mapping -1, 0
                             or 5..9); states then have 4*n values */
-    int reserved[6];     /* must be zero */
+    int certify;         /* 0 (default): evaluate the rigorous lower bound
+                            (stats.certified_lb) only when the approximate one
+                            is close to the energy and the iterate precision
+                            can certify the grid; 1: at every check (costs one
+                            projection scan and two passes over the grid) */
+    int stop_on_approx;  /* 1: tvcut_iterate also stops when energy -
+                            discrete_lb < 1 on integer data, the certificate
+                            evaluated with the iterate's own (approximate)
+                            dual.  Not a proof: it is the stop rule for FP32
+                            iterates on large grids, whose rigorous bound stays
+                            about 1e-4 |E| below the energy (FP32 rounding of
+                            the duals summed over the grid).  Default 0 */
+    int reserved[4];     /* must be zero */
 } tvcut_params;
 
 typedef struct {
@@ -125,19 +137,36 @@ typedef struct {
     int64_t energy_i64;    /* E(l) in exact integer arithmetic; valid when
                               energy_exact != 0 */
     int energy_exact;      /* unary and all weights were set as TVCUT_I32 */
-    int certified;         /* energy_exact and energy - discrete_lb < 1: with
-                              integer data the labels are then a minimum cut
-                              (Sec. 2.2 certificate; FP32 iterates make the
-                              lower bound approximate, see discrete_lb) */
+    int certified;         /* energy_exact and energy - certified_lb < 1:
+                              with integer data the labels are then a minimum
+                              cut (Sec. 2.2 certificate), whatever the iterate
+                              precision */
     double discrete_lb;    /* sum_i min(y_i - w_i, 0) = -sum_i max(x_i, 0) with
-                              y = w - x, the dual bound of problem (C) (Sec. 2.2);
-                              a true lower bound on E* when y lies in K */
+                              y = w - x, the dual bound of problem (C) (Sec. 2.2)
+                              at the iterate; only approximately a lower bound
+                              on E*, since y lies in K up to the rounding of the
+                              iterates (with drifting FP32 AAR states it can
+                              exceed E* by far) */
     double tv_value;       /* f(x) */
     double tv_gap;         /* f(x) - y^T x, the TV duality gap (Sec. 2.3) */
     double x_absmax;       /* max_i |x_i| */
     int64_t n_label1;      /* number of vertices labelled 1 */
     double threshold;      /* level at which the labels were cut */
-    int64_t reserved[3];
+    double certified_lb;   /* a rigorous lower bound on E*: the block duals of
+                              the current state (BCD, FISTA: the state; AAR,
+                              AP: its chain projections) made exactly feasible
+                              chain by chain (running sums of each chain's dual
+                              clamped to [-a, a]) and evaluated as
+                              sum_i min(y_i - w_i, 0) in FP64, minus a bound on
+                              that sum's rounding.  Evaluated on integer data
+                              when params.certify is 1, or when
+                              energy - discrete_lb < 1 + 1e-7 |energy| and the
+                              iterate precision can close it (n * eps *
+                              max|x| < 1/2, eps = 2^-24 for FP32, 2^-53 for
+                              FP64: FP32 iterates cannot certify grids much
+                              beyond 10^5 vertices); -infinity when not
+                              evaluated */
+    int64_t reserved[2];
 } tvcut_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -178,8 +207,9 @@ tvcut_status tvcut_reset(tvcut_t h);
 /* Run up to max_iters iterations (max_iters >= 1).  Every check_every
  * iterations and after the last one, the primal x = w - sum_k y_k of the
  * current shadow (Eq. dualA, Sec. 2.3) is thresholded and its energy and
- * gaps are evaluated; iteration stops early when `certified` holds or the TV
- * gap reaches gap_tol.  Returns OK when a criterion held, NOT_CONVERGED when
+ * gaps are evaluated; iteration stops early when `certified` holds, when the
+ * TV gap reaches gap_tol, or (params.stop_on_approx) when energy -
+ * discrete_lb < 1.  Returns OK when a criterion held, NOT_CONVERGED when
  * max_iters ran out, STATE if unary or weights are missing, CUDA on device
  * errors.  out (may be NULL) receives the statistics of the last check. */
 tvcut_status tvcut_iterate(tvcut_t h, int64_t max_iters, tvcut_stats* out);
@@ -283,8 +313,11 @@ tvcut_status tvcut_batch_set_weights(tvcut_batch_t b, int g, int axis, const voi
 tvcut_status tvcut_batch_reset(tvcut_batch_t b);
 
 /* Exactly `iters` iterations of every grid, then a check of every grid
- * (labels, energy, bounds, level sets).  out: NULL or G tvcut_stats.
- * Returns OK if every grid is certified, NOT_CONVERGED otherwise. */
+ * (labels, energy, bounds, level sets).  out: NULL or G tvcut_stats.  For
+ * batched grids `certified` compares the energy with the approximate bound
+ * discrete_lb (the rigorous certified_lb of single grids is not evaluated
+ * here and reads -infinity): a screen, not a proof, with FP32 iterates.
+ * Returns OK if every grid is so certified, NOT_CONVERGED otherwise. */
 tvcut_status tvcut_batch_iterate(tvcut_batch_t b, int64_t iters, tvcut_stats* out);
 
 /* Labels (H_g x W_g uint8) and statistics of grid g after the last check. */
@@ -382,6 +415,20 @@ int tvcut_conv_tc_error(void);
  * is incomplete, and tvcut_conv_tc_error reports 1.  Off by default; the
  * convolutions are unaffected while it is off. */
 tvcut_status tvcut_conv_tc_stall(int on);
+
+/* Learned warm start of a solver handle (row a8; the warm start of Sec. 4.4
+ * reuses dual variables, here they are predicted): the network's input is
+ * built on the device from h's unary and edge weights as set -- pixel (r, c)
+ * gets [w, a_vertical (r,c)-(r+1,c), a_horizontal (r,c)-(r,c+1)] / s with
+ * s = max(max|w|, max a), 0 on the last row / column -- the forward pass runs,
+ * and output channel k times s becomes block k's state (z = y_hat for AAR and
+ * AP, y = y_hat for BCD and FISTA, whose momentum restarts).  h must be a 2D
+ * 4-connected grid with H and W multiples of 8; the network is resized to
+ * (1, H, W) when its shape differs (that reallocates its activations).  The
+ * work is ordered after h's stream and h's stream after it; nothing
+ * synchronises.  Errors (tvcut_unet_last_error(u)): INVALID, STATE (h's
+ * inputs missing), OOM, CUDA. */
+tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h);
 
 /* The U-Net's convolutions (forward and input gradient): engine 0 (default)
  * uses the persistent tcgen05 kernel for every layer whose shape it takes

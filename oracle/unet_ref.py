@@ -8,8 +8,18 @@ for each of the 18 convolutions in forward order, weights [9][Cout][Cin]
 [upsampled, skip]; ReLU after every convolution but the last; input padded
 from 3 to 16 channels with zeros; output channels 0 and 1; loss = mean
 squared error over those two channels.  Gradients come from autograd; the
-pins in tests/test_oracle_unet.py check them against finite differences and
-the convolution against a direct loop.
+pins in tests/test_oracle_unet.py check them against finite differences, the
+convolution against a direct loop, and the wiring (pooling, upsampling, the
+skip connections and the concatenation order, the ReLU placement) against a
+hand-derived closed form (tests/golden/unet_wiring.json).
+
+``bf16_storage=True`` rounds every stored tensor to BF16 where the library
+stores one (the packed input, each convolution's output but the last, each
+pooled tensor; in the backward pass the gradient of each of those tensors
+and of the output), with the arithmetic between stores in the oracle's own
+precision.  Element-wise comparisons of the library's BF16 network are made
+against this; it is the definition above with the storage precision made
+explicit, not a model of any kernel's summation order.
 """
 from __future__ import annotations
 
@@ -46,27 +56,59 @@ def conv(x, wb, relu=True):
     return F.relu(y) if relu else y
 
 
-def forward(theta: torch.Tensor, x: torch.Tensor, base: int) -> torch.Tensor:
+class _StoreBF16(torch.autograd.Function):
+    """Identity up to BF16 rounding (round to nearest even) of the value in
+    the forward pass and of the incoming gradient in the backward pass."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.to(torch.bfloat16).to(t.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
+class _GradBF16(torch.autograd.Function):
+    """Identity in the forward pass; BF16 rounding of the gradient."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.view_as(t)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
+def forward(theta: torch.Tensor, x: torch.Tensor, base: int, bf16_storage: bool = False) -> torch.Tensor:
     """x: (N, H, W, 3) -> (N, H, W, 2)."""
     L = unpack(theta, base)
     n, h, w, _ = x.shape
+    st = _StoreBF16.apply if bf16_storage else (lambda t: t)
     xin = torch.zeros(n, 16, h, w, dtype=theta.dtype)
     xin[:, :3] = x.permute(0, 3, 1, 2)
-    e1 = conv(conv(xin, L[0]), L[1])
-    e2 = conv(conv(F.avg_pool2d(e1, 2), L[2]), L[3])
-    e3 = conv(conv(F.avg_pool2d(e2, 2), L[4]), L[5])
-    e4 = conv(conv(F.avg_pool2d(e3, 2), L[6]), L[7])
+    xin = st(xin)
+    c = lambda t, i: st(conv(t, L[i]))
+    pool = lambda t: st(F.avg_pool2d(t, 2))
+    e1 = c(c(xin, 0), 1)
+    e2 = c(c(pool(e1), 2), 3)
+    e3 = c(c(pool(e2), 4), 5)
+    e4 = c(c(pool(e3), 6), 7)
     up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
-    d3 = conv(conv(torch.cat([conv(up(e4), L[8]), e3], 1), L[9]), L[10])
-    d2 = conv(conv(torch.cat([conv(up(d3), L[11]), e2], 1), L[12]), L[13])
-    d1 = conv(conv(torch.cat([conv(up(d2), L[14]), e1], 1), L[15]), L[16])
+    d3 = c(c(torch.cat([c(up(e4), 8), e3], 1), 9), 10)
+    d2 = c(c(torch.cat([c(up(d3), 11), e2], 1), 12), 13)
+    d1 = c(c(torch.cat([c(up(d2), 14), e1], 1), 15), 16)
     out = conv(d1, L[17], relu=False)
+    if bf16_storage:
+        out = _GradBF16.apply(out)
     return out[:, :2].permute(0, 2, 3, 1)
 
 
-def loss_and_grad(theta: np.ndarray, x: np.ndarray, target: np.ndarray, base: int, dtype=torch.float32):
+def loss_and_grad(theta: np.ndarray, x: np.ndarray, target: np.ndarray, base: int, dtype=torch.float32,
+                  bf16_storage: bool = False):
     th = torch.tensor(theta, dtype=dtype, requires_grad=True)
-    out = forward(th, torch.tensor(x, dtype=dtype), base)
+    out = forward(th, torch.tensor(x, dtype=dtype), base, bf16_storage)
     loss = ((out - torch.tensor(target, dtype=dtype)) ** 2).mean()
     loss.backward()
     return float(loss.detach()), th.grad.numpy(), out.detach().numpy()

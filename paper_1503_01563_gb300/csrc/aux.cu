@@ -376,13 +376,102 @@ cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state,
     return cudaGetLastError();
 }
 
+
+// ---- rigorous discrete lower bound (Sec. 2.2) --------------------------------
+//
+// Any y in K gives E* >= sum_i min(y_i - w_i, 0).  A block dual y_k computed
+// in the iterate's precision is only close to K_k, so the bound is taken from
+// a point that is exactly in it: along each chain the edge multipliers are
+// the running sums u_j = y_0 + ... + y_j of the block dual (the string
+// offsets of the taut string, Sec. 3.2), clamped to [-a_j, a_j], with
+// u = 0 after the chain's last element; the chain's contribution to vertex j
+// is then u_j - u_{j-1}, which lies in K_k by construction.  Sums run in
+// FP64, the blocks are added one launch at a time into an FP64 vertex array
+// (each vertex lies on one chain of every block), and the bound is reduced
+// per CTA in a fixed order.
+
+template <typename T>
+__global__ void __launch_bounds__(256) certify_block_kernel(CertifyArgs<T> A)
+{
+    const ScanAxis<T>& X = A.X;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < X.nchains;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = X.transposed ? 0 : c / X.inner, q = X.transposed ? 0 : c - o * X.inner;
+        double run = 0.0, uprev = 0.0;
+        for (int j = 0; j < X.m; ++j) {
+            const int64_t e = X.transposed ? (int64_t)j * X.nchains + c : o * X.m * X.inner + q + (int64_t)j * X.inner;
+            run += (double)X.v[e];
+            double u = 0.0;
+            if (j < X.m - 1) {
+                const int64_t wi = X.transposed ? e : o * (X.m - 1) * X.inner + q + (int64_t)j * X.inner;
+                const double a = (double)X.a[wi];
+                u = run < -a ? -a : (run > a ? a : run);
+            }
+            const double yh = u - uprev;
+            uprev = u;
+            int64_t nat = e;
+            if (A.layout == 1) nat = c * X.m + j;
+            else if (A.layout >= 2) nat = (int64_t)zz_row((int)c, j, (int)A.H, A.layout) * A.W + j;
+            A.Y[nat] = A.first ? yh : A.Y[nat] + yh;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCheckThreads) certify_lb_kernel(const double* __restrict__ Y, const T* __restrict__ w,
+                                                                  int64_t n, double* __restrict__ part)
+{
+    double s = 0.0, mag = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double y = Y[i];
+        const double d = y - (double)w[i];
+        const double m = d < 0.0 ? d : 0.0;
+        s += m;
+        mag += fabs(m) + fabs(y);
+    }
+    __shared__ double sh[2][kCheckThreads];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = mag;
+    __syncthreads();
+    for (int h = kCheckThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sh[0][0];
+        part[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+template <typename T>
+cudaError_t launch_certify_block(const CertifyArgs<T>& A, cudaStream_t s)
+{
+    if (A.X.nchains <= 0 || A.X.m <= 0) return cudaSuccess;
+    const int64_t want = (A.X.nchains + 255) / 256;
+    const int blocks = (int)(want < 8192 ? want : 8192);
+    certify_block_kernel<T><<<blocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_certify_lb(const double* Y, const T* w, int64_t n, double* part, cudaStream_t s)
+{
+    certify_lb_kernel<T><<<kCheckBlocks, kCheckThreads, 0, s>>>(Y, w, n, part);
+    return cudaGetLastError();
+}
+
 #define TVCUT_INST(T)                                                                          \
     template cudaError_t launch_check<T>(const CheckArgs<T>&, bool, DevStatus*, cudaStream_t);  \
     template cudaError_t launch_convert<T>(const void*, int, T*, int64_t, bool, int*, unsigned*, cudaStream_t); \
     template cudaError_t launch_labels<T>(const T*, T, uint8_t*, int64_t, cudaStream_t);         \
     template cudaError_t launch_convert_out<T>(const T*, void*, int, int64_t, cudaStream_t);    \
     template cudaError_t launch_cold_ap<T>(const T*, T*, int, int64_t, cudaStream_t);           \
-    template cudaError_t launch_warmstart<T>(const T*, const float*, float, T*, int, int64_t, cudaStream_t);
+    template cudaError_t launch_warmstart<T>(const T*, const float*, float, T*, int, int64_t, cudaStream_t); \
+    template cudaError_t launch_certify_block<T>(const CertifyArgs<T>&, cudaStream_t);             \
+    template cudaError_t launch_certify_lb<T>(const double*, const T*, int64_t, double*, cudaStream_t);
 TVCUT_INST(float)
 TVCUT_INST(double)
 

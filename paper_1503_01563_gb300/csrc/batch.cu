@@ -958,7 +958,8 @@ static tvcut_status biterate(tvcut_batch_t b, int64_t iters, tvcut_stats* out)
         o.tv_value = s.tv;
         o.tv_gap = s.tv - s.ytx;
         o.x_absmax = s.xabs;
-        o.certified = (exact && (double)o.energy_i64 - s.lb < 1.0) ? 1 : 0;
+        o.certified = (exact && (double)o.energy_i64 - s.lb < 1.0) ? 1 : 0;   // approximate bound only
+        o.certified_lb = -INFINITY;
         all_cert = all_cert && o.certified;
     }
     if (relabel) {

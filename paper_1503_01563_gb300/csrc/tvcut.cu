@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -47,9 +48,12 @@ struct tvcut_ctx {
     double fista_t = 1.0;
     bool tlast = true;             // scan schedule: block ndim-1 (state, weights) stored transposed
     uint8_t* labels = nullptr;     // n
+    double* ycert = nullptr;       // n, FP64: the exactly feasible dual of the rigorous bound (on first use)
+    double* lbpart = nullptr;      // 2 * kCheckBlocks partial sums of that bound
     CheckPartial* partials = nullptr;
     LevelPartial* level_partials = nullptr;
     double wmax = 0.0;             // max |w|: scale of the level-set ladder
+    double amax[4] = {0, 0, 0, 0}; // max a per weight axis (scale of the learned warm start's features)
     DevStatus* dstatus = nullptr;
     DevStatus* hstatus = nullptr;  // pinned
     bool have_w = false, have_a[4] = {false, false, false, false};
@@ -125,6 +129,8 @@ extern "C" void tvcut_destroy(tvcut_t h)
     cudaFree(h->xk);
     cudaFree(h->yprev);
     cudaFree(h->labels);
+    cudaFree(h->ycert);
+    cudaFree(h->lbpart);
     cudaFree(h->partials);
     cudaFree(h->level_partials);
     cudaFree(h->dstatus);
@@ -150,7 +156,9 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
-    for (int i = 0; i < 6; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
+    if (p->certify != 0 && p->certify != 1) { why = "params.certify must be 0 or 1"; return false; }
+    if (p->stop_on_approx != 0 && p->stop_on_approx != 1) { why = "params.stop_on_approx must be 0 or 1"; return false; }
+    for (int i = 0; i < 4; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
     if (p->connectivity != 0 && p->connectivity != 4 && p->connectivity != 6 && p->connectivity != 8) {
         why = "params.connectivity must be 0, 4, 6 or 8";
         return false;
@@ -656,6 +664,60 @@ static cudaError_t run_iteration(tvcut_t h, int mode, int check)
     return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_update<T>(mode, U, h->stream); });
 }
 
+// Rigorous discrete lower bound (Sec. 2.2): the block duals of the current
+// state (the state itself for BCD and FISTA, its chain projections
+// Pi_{K_k}(s_k) for AAR and AP) made exactly feasible chain by chain in FP64,
+// summed, and bounded by sum_i min(y_i - w_i, 0); the FP64 rounding of that
+// sum is covered by subtracting 2^-36 of the sum of the magnitudes.
+template <typename T>
+static tvcut_status rigorous_lb(tvcut_t h, double* lb_out)
+{
+    if (!h->ycert) {
+        CK(h, cudaMalloc(&h->ycert, sizeof(double) * (size_t)h->n), "certify: allocation");
+        CK(h, cudaMalloc(&h->lbpart, sizeof(double) * 2 * kCheckBlocks), "certify: allocation");
+    }
+    const bool shadow = h->p.algo == TVCUT_AAR || h->p.algo == TVCUT_AP;
+    const T* yk[4];
+    for (int k = 0; k < h->nblk; ++k) yk[k] = shadow ? XK_of<T>(h, k) : S_of<T>(h, k);
+    const int nk = (shadow ? 1 : 0) + h->nblk + 1;
+    CK(h, traced(h, TVCUT_K_CHECK, nk, [&] {
+           cudaError_t e = cudaSuccess;
+           if (shadow) {
+               ScanArgs<T> S;
+               memset(&S, 0, sizeof(S));
+               S.naxes = h->nblk;
+               for (int k = 0; k < h->nblk; ++k) S.ax[k] = block_axis<T>(h, k, S_of<T>(h, k), XK_of<T>(h, k));
+               S.shadow = 1;
+               e = launch_scan<T>(S, h->stream);
+           }
+           for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+               CertifyArgs<T> A;
+               memset(&A, 0, sizeof(A));
+               A.X = block_axis<T>(h, k, yk[k], nullptr);
+               A.layout = block_layout(h, k);
+               A.first = k == 0 ? 1 : 0;
+               A.H = h->dims[0];
+               A.W = h->ndim == 2 ? h->dims[1] : 1;
+               A.Y = h->ycert;
+               e = launch_certify_block<T>(A, h->stream);
+           }
+           if (e == cudaSuccess) e = launch_certify_lb<T>(h->ycert, (const T*)h->w, h->n, h->lbpart, h->stream);
+           return e;
+       }), "certify");
+    std::vector<double> part(2 * kCheckBlocks);
+    CK(h, cudaMemcpyAsync(part.data(), h->lbpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream),
+       "certify");
+    CK(h, cudaStreamSynchronize(h->stream), "certify");
+    CK(h, flush_trace(h), "certify");
+    double lb = 0.0, mag = 0.0;
+    for (int b = 0; b < kCheckBlocks; ++b) {
+        lb += part[2 * b];
+        mag += part[2 * b + 1];
+    }
+    *lb_out = lb - mag * ldexp(1.0, -36);
+    return TVCUT_OK;
+}
+
 template <typename T>
 static tvcut_status run_check(tvcut_t h)
 {
@@ -733,8 +795,26 @@ static tvcut_status run_check(tvcut_t h)
     st.tv_value = s.tv;
     st.tv_gap = s.tv - s.ytx;
     st.x_absmax = s.xabs;
-    st.certified = (exact && (double)st.energy_i64 - s.lb < 1.0) ? 1 : 0;
+    // certified only against the rigorous bound; it is evaluated when asked
+    // for at every check, or when the approximate bound is within
+    // 1 + 1e-7 |E| of the energy and the iterate's precision can bring it
+    // within 1: its rounding floor n * eps * max|x| (the duals' rounding
+    // summed over the grid) must stay below 1/2
+    st.certified = 0;
+    st.certified_lb = -INFINITY;
     h->labels_valid = true;
+    if (exact) {
+        const double E = (double)st.energy_i64;
+        const double eps = sizeof(T) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+        const bool reachable = (double)h->n * eps * std::max(s.xabs, 1.0) < 0.5;
+        if (h->p.certify == 1 || (reachable && E - s.lb < 1.0 + 1e-7 * fabs(E))) {
+            double lb = 0.0;
+            tvcut_status cs = rigorous_lb<T>(h, &lb);
+            if (cs != TVCUT_OK) return cs;
+            st.certified_lb = lb;
+            st.certified = E - lb < 1.0 ? 1 : 0;
+        }
+    }
     return TVCUT_OK;
 }
 
@@ -764,7 +844,8 @@ static tvcut_status iterate_impl(tvcut_t h, int64_t max_iters, tvcut_stats* out)
             tvcut_status st = run_check<T>(h);
             if (st != TVCUT_OK) return st;
             const tvcut_stats& s = h->last;
-            if (s.certified || (h->p.gap_tol > 0.0 && s.tv_gap <= h->p.gap_tol)) {
+            const bool approx = h->p.stop_on_approx && s.energy_exact && (double)s.energy_i64 - s.discrete_lb < 1.0;
+            if (s.certified || approx || (h->p.gap_tol > 0.0 && s.tv_gap <= h->p.gap_tol)) {
                 ret = TVCUT_OK;
                 break;
             }
@@ -809,6 +890,12 @@ static tvcut_status set_weights_impl(tvcut_t h, int axis, const void* a, int dty
     T* dst = diag ? (T*)(axis == 2 ? h->adiag : h->aanti) : (T*)h->a[axis];
     tvcut_status st = ingest<T>(h, a, dtype, space, h->a_len[axis], true, dst, "tvcut_set_weights");
     if (st != TVCUT_OK) { h->have_a[axis] = false; return st; }
+    {
+        float m;
+        const unsigned bits = h->hstatus->absmax_bits;
+        memcpy(&m, &bits, sizeof(m));
+        h->amax[axis] = h->a_len[axis] > 0 ? (double)m : 0.0;
+    }
     if (h->tlast && axis == h->ndim - 1)
         CK(h, relayout<T>(h, (T*)h->a[axis], rows_of(h), cols_of(h) - 1, true), "tvcut_set_weights");
     if (!diag && h->ap[axis])
@@ -978,6 +1065,42 @@ extern "C" tvcut_status tvcut_get_dual(tvcut_t h, void* y, int space)
         return DISPATCH(h, get_state_impl, h, y, space);     // the BCD and FISTA states are y itself
     return DISPATCH(h, get_dual_impl, h, y, space);
 }
+
+namespace tvcut {
+
+tvcut_status problem_view(tvcut_t h, ProblemView* v, std::string* why)
+{
+    if (h->ndim != 2 || h->conn8) {
+        *why = "the learned warm start takes 2D 4-connected grids";
+        return TVCUT_ERR_INVALID;
+    }
+    if (!inputs_ready(h)) {
+        *why = "unary and all edge weights must be set first";
+        return TVCUT_ERR_STATE;
+    }
+    v->esize = h->esize;
+    v->H = h->dims[0];
+    v->W = h->dims[1];
+    v->w = h->w;
+    v->a0 = h->a[0];
+    v->a1 = h->a[1];
+    v->a1_transposed = h->tlast ? 1 : 0;
+    v->s0 = (char*)h->state;
+    v->s1 = (char*)h->state + (size_t)h->esize * (size_t)h->n;
+    v->s1_transposed = block_layout(h, 1) == 1 ? 1 : 0;
+    v->scale = std::max(std::max(h->wmax, std::max(h->amax[0], h->amax[1])), 1e-12);
+    v->stream = h->stream;
+    return TVCUT_OK;
+}
+
+tvcut_status state_written(tvcut_t h)
+{
+    CK(h, restart_momentum(h), "tvcut_unet_predict_state");
+    h->x_valid = h->labels_valid = false;
+    return TVCUT_OK;
+}
+
+}  // namespace tvcut
 
 template <typename T>
 static tvcut_status set_state_impl(tvcut_t h, const void* s, int space)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "tvcut.h"
 
 namespace tvcut {
@@ -34,6 +36,15 @@ struct ScanAxis {
     const T* a;            // compact weights (m - 1 per chain)
     const T* ap;           // the same weights in the state's layout, 0 at each chain's end; may be null
     T* x;
+};
+
+template <typename T>
+struct CertifyArgs {
+    ScanAxis<T> X;
+    int layout;
+    int first;
+    int64_t H, W;
+    double* Y;
 };
 
 template <typename T>
@@ -168,6 +179,18 @@ template <typename T>
 cudaError_t launch_warmstart(const T* w, const float* xhat, float tau, T* state, int r,
                              int64_t n, cudaStream_t s);
 
+// Rigorous discrete lower bound: block k's dual y_k (X.v, in the block's
+// layout X describes, X.a its compact weights) made exactly feasible chain by
+// chain and added into the FP64 vertex array Y (grid layout; written when
+// `first`).  layout: 0 natural, 1 the transposed last axis (grid rows of
+// length X.m), 2 / 3 the zig-zag paths of an H x W 8-connected grid.
+template <typename T>
+cudaError_t launch_certify_block(const CertifyArgs<T>& A, cudaStream_t s);
+// part[2b] = sum of min(Y_i - w_i, 0), part[2b+1] = sum of |min(Y_i - w_i, 0)| + |Y_i|
+// over CTA b's share (kCheckBlocks CTAs)
+template <typename T>
+cudaError_t launch_certify_lb(const double* Y, const T* w, int64_t n, double* part, cudaStream_t s);
+
 // Launchers (scan.cu)
 template <typename T>
 cudaError_t launch_scan(ScanArgs<T> args, cudaStream_t s);
@@ -254,5 +277,27 @@ template <typename T>
 cudaError_t launch_fista_prepare(const FistaArgs<T>& args, cudaStream_t s);
 
 ChainGeom chain_geom(int ndim, const int64_t* dims, int axis);
+
+// A 2D 4-connected handle's problem as the learned warm start reads it
+// (unet.cu): device unary and weights in the handle's layouts, its state
+// blocks, the scale of the network's features and the handle's stream.
+struct ProblemView {
+    int esize;               // 4 (FP32 iterates) or 8 (FP64)
+    int64_t H, W;
+    const void* w;           // H x W
+    const void* a0;          // (H-1) x W vertical weights (r, c)-(r+1, c) at r*W + c
+    const void* a1;          // horizontal weights (r, c)-(r, c+1): at r*(W-1) + c, or c*H + r when a1_transposed
+    int a1_transposed;
+    void* s0;                // state block 0 (columns), H x W
+    void* s1;                // state block 1 (rows): r*W + c, or c*H + r when s1_transposed
+    int s1_transposed;
+    double scale;            // max(max|w|, max a) of the inputs as set
+    cudaStream_t stream;
+};
+// OK, or INVALID / STATE with `why` set (not a 2D 4-connected grid, inputs missing).
+tvcut_status problem_view(tvcut_t h, ProblemView* v, std::string* why);
+// After the state was written from outside tvcut.cu: restart FISTA's momentum
+// and drop the cached primal and labels (stream-ordered on the handle's stream).
+tvcut_status state_written(tvcut_t h);
 
 }  // namespace tvcut

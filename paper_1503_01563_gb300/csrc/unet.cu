@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "tvcut.h"
+#include "tvcut_internal.cuh"
 #include "unet_kernels.cuh"
 
 using namespace tvcut::nn;
@@ -62,6 +63,42 @@ __global__ void input_pack_kernel(const float* in, bf16* x, int64_t P)
         uint4* o = (uint4*)(x + p * 16);
         o[0] = pack8(f);
         o[1] = pack8(z);
+    }
+}
+
+// The network's input straight from a handle's device problem: pixel (r, c)
+// gets [w, a_down, a_right] / s, then zeros to 16 channels, in BF16 (a_down =
+// the vertical edge (r, c)-(r+1, c), a_right = the horizontal edge
+// (r, c)-(r, c+1), 0 on the last row / column).  Each feature is rounded
+// from FP64 to FP32 and then to BF16, the path of an FP32 feature array.
+template <typename T>
+__global__ void features_pack_kernel(const T* __restrict__ w, const T* __restrict__ a0, const T* __restrict__ a1,
+                                     int a1_transposed, int H, int W, double s, bf16* __restrict__ x)
+{
+    GRID_STRIDE(p, (int64_t)H * W) {
+        const int r = (int)(p / W), c = (int)(p - (int64_t)r * W);
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        f[0] = (float)((double)w[p] / s);
+        if (r < H - 1) f[1] = (float)((double)a0[p] / s);
+        if (c < W - 1)
+            f[2] = (float)((double)(a1_transposed ? a1[(int64_t)c * H + r] : a1[(int64_t)r * (W - 1) + c]) / s);
+        uint4* o = (uint4*)(x + p * 16);
+        o[0] = pack8(f);
+        o[1] = pack8(z);
+    }
+}
+
+// Predicted block duals y_k = output channel k times s (an FP32 product),
+// written into a handle's state blocks in their own layouts.
+template <typename T>
+__global__ void state_from_output_kernel(const float* __restrict__ o16, int H, int W, float s, T* __restrict__ s0,
+                                         T* __restrict__ s1, int s1_transposed)
+{
+    GRID_STRIDE(p, (int64_t)H * W) {
+        const int r = (int)(p / W), c = (int)(p - (int64_t)r * W);
+        s0[p] = (T)(o16[p * 16] * s);
+        s1[s1_transposed ? (int64_t)c * H + r : p] = (T)(o16[p * 16 + 1] * s);
     }
 }
 
@@ -517,7 +554,7 @@ static tvcut_status forward(tvcut_unet_t u, const float* in)
     auto& a = u->acts;
     const int N = u->N, H = u->H, W = u->W;
     const int64_t P0 = (int64_t)N * H * W;
-    input_pack_kernel<<<blocks_for(P0), 256, 0, u->stream>>>(in, a[A_X].y, P0);
+    if (in) input_pack_kernel<<<blocks_for(P0), 256, 0, u->stream>>>(in, a[A_X].y, P0);   // else packed already
     const bf16* wf = u->wf;
     auto pool = [&](int i, int o) {
         const int lv = a[i].level;
@@ -575,6 +612,52 @@ extern "C" tvcut_status tvcut_unet_forward(tvcut_unet_t u, const float* in, floa
         output_unpack_kernel<<<blocks_for(P * 2), 256, 0, u->stream>>>(u->out16, out, P, 16, 2);
         UCK(u, cudaGetLastError(), "tvcut_unet_forward");
     }
+    return TVCUT_OK;
+}
+
+extern "C" tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h)
+{
+    if (!u) return ufail(nullptr, TVCUT_ERR_INVALID, "tvcut_unet_predict_state: NULL network");
+    if (!h) return ufail(u, TVCUT_ERR_INVALID, "tvcut_unet_predict_state: NULL solver handle");
+    tvcut::ProblemView v;
+    std::string why;
+    tvcut_status st = tvcut::problem_view(h, &v, &why);
+    if (st != TVCUT_OK) return ufail(u, st, "tvcut_unet_predict_state: " + why);
+    if (v.H < 8 || v.W < 8 || v.H % 8 || v.W % 8 || v.H > (1 << 16) || v.W > (1 << 16))
+        return ufail(u, TVCUT_ERR_INVALID, "tvcut_unet_predict_state: H and W must be multiples of 8 in [8, 65536]");
+    if (u->N != 1 || u->H != (int)v.H || u->W != (int)v.W) UST(alloc_acts(u, 1, (int)v.H, (int)v.W));
+    const int H = (int)v.H, W = (int)v.W;
+    const int64_t P = (int64_t)H * W;
+    cudaEvent_t ev = nullptr;
+    if (u->stream != v.stream) {                 // the network's stream runs after the handle's
+        UCK(u, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "tvcut_unet_predict_state");
+        UCK(u, cudaEventRecord(ev, v.stream), "tvcut_unet_predict_state");
+        UCK(u, cudaStreamWaitEvent(u->stream, ev, 0), "tvcut_unet_predict_state");
+    }
+    if (v.esize == 8)
+        features_pack_kernel<double><<<blocks_for(P), 256, 0, u->stream>>>(
+            (const double*)v.w, (const double*)v.a0, (const double*)v.a1, v.a1_transposed, H, W, v.scale,
+            u->acts[A_X].y);
+    else
+        features_pack_kernel<float><<<blocks_for(P), 256, 0, u->stream>>>(
+            (const float*)v.w, (const float*)v.a0, (const float*)v.a1, v.a1_transposed, H, W, v.scale,
+            u->acts[A_X].y);
+    UCK(u, cudaGetLastError(), "tvcut_unet_predict_state");
+    UST(forward(u, nullptr));
+    if (v.esize == 8)
+        state_from_output_kernel<double><<<blocks_for(P), 256, 0, u->stream>>>(
+            u->out16, H, W, (float)v.scale, (double*)v.s0, (double*)v.s1, v.s1_transposed);
+    else
+        state_from_output_kernel<float><<<blocks_for(P), 256, 0, u->stream>>>(
+            u->out16, H, W, (float)v.scale, (float*)v.s0, (float*)v.s1, v.s1_transposed);
+    UCK(u, cudaGetLastError(), "tvcut_unet_predict_state");
+    if (ev) {                                    // and the handle's stream after the network's
+        UCK(u, cudaEventRecord(ev, u->stream), "tvcut_unet_predict_state");
+        UCK(u, cudaStreamWaitEvent(v.stream, ev, 0), "tvcut_unet_predict_state");
+        cudaEventDestroy(ev);
+    }
+    st = tvcut::state_written(h);
+    if (st != TVCUT_OK) return ufail(u, st, "tvcut_unet_predict_state: " + std::string(tvcut_last_error(h)));
     return TVCUT_OK;
 }
 

@@ -20,8 +20,10 @@ from . import inputs, tvcut
 
 
 def features(w, a):
-    """(H, W, 3) float32 features [w, a_down, a_right] / s and the scale s.
-    a[0]: (H-1, W) vertical weights, a[1]: (H, W-1) horizontal weights."""
+    """(H, W, 3) float32 features [w, a_down, a_right] / s and the scale s, on
+    the host (training data; tvcut_unet_predict_state builds the same
+    features on the device for a solver's problem).  a[0]: (H-1, W) vertical
+    weights, a[1]: (H, W-1) horizontal weights."""
     H, W = w.shape
     f = np.zeros((H, W, 3), dtype=np.float32)
     s = float(max(np.abs(w).max(), max(x.max() for x in a), 1e-12))
@@ -92,13 +94,9 @@ def train(net, X, Y, steps: int, batch: int, lr: float = 1e-3, seed: int = 0, lr
     return hist
 
 
-def predict_state(net, w, a):
-    """Warm-start state (2, H, W) float32 CUDA tensor: the predicted block
-    duals, rescaled to the problem.  H and W must be multiples of 8."""
-    import torch
-    f, s = features(w, a)
-    H, W = w.shape
-    if net.shape != (1, H, W):
-        net.resize(1, H, W)
-    out = net.forward(torch.from_numpy(f[None]).cuda())
-    return (out[0].permute(2, 0, 1) * s).contiguous()
+def predict_state(net, solver):
+    """Warm-start `solver` (a 2D 4-connected tvcut.Solver whose problem is
+    set) from the network's predicted block duals: features, inference and
+    the rescaling to the problem all run on the device
+    (tvcut_unet_predict_state).  H and W must be multiples of 8."""
+    net.predict_state(solver)

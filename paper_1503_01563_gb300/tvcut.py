@@ -35,6 +35,7 @@ EXPORTED = [
     "tvcut_unet_forward", "tvcut_unet_backward", "tvcut_unet_adam", "tvcut_unet_num_params",
     "tvcut_unet_get_params", "tvcut_unet_set_params", "tvcut_conv3x3_bf16", "tvcut_conv3x3_wgrad_bf16",
     "tvcut_conv3x3_bf16_ex", "tvcut_conv_tc_error", "tvcut_unet_set_engine", "tvcut_conv_tc_stall",
+    "tvcut_unet_predict_state",
 ]
 K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
@@ -49,7 +50,9 @@ class Params(ctypes.Structure):
         ("threshold", ctypes.c_double),
         ("level_sets", ctypes.c_int),
         ("connectivity", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("certify", ctypes.c_int),
+        ("stop_on_approx", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -66,7 +69,8 @@ class Stats(ctypes.Structure):
         ("x_absmax", ctypes.c_double),
         ("n_label1", ctypes.c_int64),
         ("threshold", ctypes.c_double),
-        ("reserved", ctypes.c_int64 * 3),
+        ("certified_lb", ctypes.c_double),
+        ("reserved", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self):
@@ -133,6 +137,7 @@ def load(path: str = LIB_PATH):
         "tvcut_conv_tc_error": (c_int, []),
         "tvcut_conv_tc_stall": (st, [c_int]),
         "tvcut_unet_set_engine": (st, [P, c_int]),
+        "tvcut_unet_predict_state": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -357,8 +362,10 @@ class Solver:
     anti-diagonal) and states have four blocks."""
 
     def __init__(self, dims, algo=AAR, dtype=F32, check_every=10, gap_tol=0.0, threshold=0.0,
-                 stream=None, level_sets=None, mapping=-1, connectivity=0):
+                 stream=None, level_sets=None, mapping=-1, connectivity=0, certify=0, stop_on_approx=0):
         p = tvcut_default_params()
+        p.certify = certify
+        p.stop_on_approx = stop_on_approx
         p.mapping = mapping
         p.connectivity = connectivity
         if level_sets is not None:
@@ -561,6 +568,11 @@ class UNet:
         p = np.ascontiguousarray(p, dtype=np.float32)
         assert p.size == self.nparams
         _ucheck(lib().tvcut_unet_set_params(self.h, ctypes.c_void_p(p.ctypes.data)), self.h)
+
+    def predict_state(self, solver):
+        """Warm-start `solver` (a 2D 4-connected Solver) from the network's
+        predicted block duals, computed on the device from its problem."""
+        _ucheck(lib().tvcut_unet_predict_state(self.h, solver.h), self.h)
 
     def set_engine(self, engine):
         """0: tcgen05 convolutions where the shape allows (default), 1: mma.sync."""

@@ -308,33 +308,49 @@ def test_errors(tv):
 
 
 # ---- full-size workloads, in the configuration the benchmark times ---------------
+#
+# FP32 iterates against the FP64 oracle at the iteration counts the benchmark
+# runs to reach the oracle-equal cut (k*), element by element.  The AAR state
+# z drifts linearly (Sec. 4.3: z^t grows like t x*/r), so its FP32 rounding
+# grows with k: measured primal errors at k* are 3.7e-5 of max|x| on the 3D
+# volume (k* = 75) and 1.1e-4 on the 2D segmentation (k* = 223; up to 1.2e-4
+# on 2048^2 grids within 415 iterations), hence the stated FP32 tolerance of
+# 2e-4 for AAR on 2D grids and 1e-4 otherwise (states: 1e-4 of max|state|;
+# measured at most 2.2e-5).  BCD and FISTA states hold the block duals
+# themselves and do not drift (primal errors below 1e-5).
 
-def test_full_size_2d_segmentation(tv, orc):
-    """1024x1024 blob segmentation, FP32 iterates: the whole primal after a
-    few iterations agrees with the FP64 oracle."""
-    dims = (1024, 1024)
-    w, a = inputs.segmentation_problem(dims, 2)
-    s = tv.Solver(dims, dtype=tv.F32, check_every=1000)
+FULL = [("volume256", (256, 256, 256), 3, 0, 75, 1e-4), ("seg1024", (1024, 1024), 2, 0, 223, 2e-4),
+        ("volume256", (256, 256, 256), 3, 2, 8, 1e-4), ("seg1024", (1024, 1024), 2, 3, 90, 1e-4)]
+
+
+@pytest.mark.parametrize("name,dims,seed,algo,k,tol", FULL)
+def test_full_size_at_bench_iterations(tv, orc, name, dims, seed, algo, k, tol):
+    """The benchmark's workload and launch configuration (FP32 iterates, the
+    automatic scan mapping) run to its k*: primal and state against the FP64
+    oracle after k/2 and k iterations, and the cut at k equals the max-flow
+    minimum exactly."""
+    if len(dims) == 3:
+        w, a = inputs.volume_problem(dims, seed)
+    else:
+        w, a = inputs.segmentation_problem(dims, seed)
+    s = tv.Solver(dims, algo=algo, dtype=tv.F32, check_every=10 ** 6)
     s.set_problem(dev(w), [dev(x) for x in a])
-    s.iterate(4)
-    _, x = orc.iterate(0, w, a, orc.cold_state(0, w), 4, nthreads=NPROC)
-    assert rel_err(s.primal(), x) < 1e-4
-    s.close()
-
-
-def test_full_size_3d_volume(tv, orc):
-    """256^3 blob volume, FP32 iterates, two iterations against the oracle."""
-    dims = (256, 256, 256)
-    w, a = inputs.volume_problem(dims, 3)
-    s = tv.Solver(dims, dtype=tv.F32, check_every=1000)
-    s.set_problem(dev(w), [dev(x) for x in a])
-    s.iterate(2)
-    _, x = orc.iterate(0, w, a, orc.cold_state(0, w), 2, nthreads=NPROC)
-    assert rel_err(s.primal(), x) < 1e-4
-    lab, st = s.cut()
-    x = s.primal(dtype=np.float32)
-    assert np.array_equal(lab, (x > np.float32(st.threshold)).astype(np.uint8))
-    assert st.energy_i64 == int(orc.energy(w, a, lab))
+    ref = orc.cold_state(algo, w)
+    done = 0
+    for kk in (k // 2, k):
+        s.iterate(kk - done)
+        if algo == 3:                                  # the oracle's FISTA momentum restarts per call
+            ref, x = orc.iterate(algo, w, a, orc.cold_state(algo, w), kk, nthreads=NPROC)
+        else:
+            ref, x = orc.iterate(algo, w, a, ref, kk - done, nthreads=NPROC)
+        done = kk
+        assert rel_err(s.primal(), x) < tol, (kk, rel_err(s.primal(), x))
+        st = s.state().astype(np.float64)
+        assert np.abs(st - ref).max() <= 1e-4 * max(np.abs(ref).max(), 1.0), kk
+    lab, stt = s.cut()
+    e_star = orc.maxflow(w, a)[1]
+    assert stt.energy_i64 == e_star
+    assert int(orc.energy(w, a, lab)) == e_star
     s.close()
 
 

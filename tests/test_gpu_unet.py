@@ -1,8 +1,20 @@
-"""Warm-start network kernels against the CPU oracle (oracle/unet_ref.py,
-PyTorch CPU FP32).  The GPU computes with BF16 weights and activations and
-FP32 accumulation, so results are compared by relative L2 error: 2e-2 for a
-single convolution, 5e-2 for the 18-layer forward pass, 1e-1 for parameter
-gradients (BF16 activation gradients through 18 layers)."""
+"""Warm-start network kernels against the CPU oracle (oracle/unet_ref.py),
+element by element.
+
+Single convolutions: the GPU multiplies BF16 inputs and weights exactly and
+accumulates in FP32, then rounds the output to BF16, so every output obeys
+|out - ref| <= 2^-8 |ref| + 2^-12 S with S = sum |w||x| + |b| over its taps
+(half a BF16 step plus a generous FP32 accumulation term); the weight
+gradient (FP32 accumulation, FP32 output) obeys |dW - ref| <= 2^-12 S_w with
+S_w = sum |x||g| over its pixels.
+
+The 18-layer network: the oracle with BF16 storage at the library's storage
+points (bf16_storage=True) is the reference; the GPU differs from it where
+FP32 summation order flips a BF16 rounding, and the flips propagate.  Every
+output obeys |out - ref| <= 8 * 2^-8 (|ref| + mean |ref|) (measured at most
+4.8), and every parameter gradient of layer l obeys
+|g - ref| <= 48 * 2^-8 (|ref| + rms_l(ref)) on 2 x 128 x 128 inputs
+(measured at most 23; BF16 activation gradients through 18 layers)."""
 import numpy as np
 import pytest
 
@@ -19,18 +31,54 @@ def tv():
     return tvcut
 
 
-def rel(a, b):
-    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def bf16_round(x):
     return torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).float().numpy()
 
 
+def conv_ref_and_scale(x, wk, b):
+    """FP64 reference of a 3x3 convolution (NHWC, weights [9][Cout][Cin],
+    zero padding) and S = sum |w||x| + |b| per output."""
+    from oracle import unet_ref
+    co, ci = wk.shape[1], wk.shape[2]
+    Wt = torch.tensor(wk, dtype=torch.float64).reshape(3, 3, co, ci).permute(2, 3, 0, 1)
+    xt = torch.tensor(x, dtype=torch.float64).permute(0, 3, 1, 2)
+    bt = torch.tensor(b, dtype=torch.float64) if b is not None else torch.zeros(co, dtype=torch.float64)
+    ref = unet_ref.F.conv2d(xt, Wt, bt, padding=1).permute(0, 2, 3, 1).numpy()
+    S = unet_ref.F.conv2d(xt.abs(), Wt.abs(), bt.abs(), padding=1).permute(0, 2, 3, 1).numpy()
+    return ref, S
+
+
+def assert_conv_bound(got, ref, S, relu):
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    d = np.abs(np.asarray(got, np.float64) - ref)
+    bound = 2 ** -8 * np.abs(ref) + 2 ** -12 * S
+    assert np.all(d <= bound), float((d / np.maximum(bound, 1e-300)).max())
+
+
+def layer_slices(base):
+    from oracle import unet_ref
+    off = 0
+    for ci, co in unet_ref.layer_shapes(base):
+        k = 9 * ci * co + co
+        yield slice(off, off + k)
+        off += k
+
+
+def bf16_weights_f32_bias(theta, base):
+    """The parameters the GPU forward pass uses: BF16 weights, FP32 biases."""
+    from oracle import unet_ref
+    th = np.asarray(theta, np.float64).copy()
+    off = 0
+    for ci, co in unet_ref.layer_shapes(base):
+        k = 9 * ci * co
+        th[off:off + k] = bf16_round(theta[off:off + k])
+        off += k + co
+    return th
+
+
 @pytest.mark.parametrize("shape", [(1, 16, 16, 16, 32), (2, 9, 13, 32, 16), (1, 8, 8, 64, 128)])
 def test_conv_forward_and_wgrad(tv, shape):
-    from oracle import unet_ref
     n, h, w, ci, co = shape
     rng = np.random.default_rng(sum(shape))
     x = bf16_round(rng.normal(size=(n, h, w, ci)))
@@ -42,20 +90,22 @@ def test_conv_forward_and_wgrad(tv, shape):
     out = torch.empty((n, h, w, co), dtype=torch.bfloat16, device="cuda")
     tv.lib().tvcut_conv3x3_bf16(xd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(), n, h, w, ci, co, 1, None)
     torch.cuda.synchronize()
-    W = torch.tensor(wk, requires_grad=True)
-    Wt = W.reshape(3, 3, co, ci).permute(2, 3, 0, 1)
-    xt = torch.tensor(x).permute(0, 3, 1, 2)
-    ref = torch.relu(unet_ref.F.conv2d(xt, Wt, torch.tensor(b), padding=1)).permute(0, 2, 3, 1)
-    assert rel(out.float().cpu().numpy(), ref.detach().numpy()) < 2e-2
-    # weight gradient of sum(ref * g) for a random g (before the ReLU: use the linear conv)
+    ref, S = conv_ref_and_scale(x, wk, b)
+    assert_conv_bound(out.float().cpu().numpy(), ref, S, relu=True)
+    # weight gradient of sum(conv(x) * g) for a random g: dW[t][o][i] = sum_p g[p][o] x[p + tap t][i]
     g = bf16_round(rng.normal(size=(n, h, w, co)))
-    lin = unet_ref.F.conv2d(xt, Wt, None, padding=1).permute(0, 2, 3, 1)
-    (lin * torch.tensor(g)).sum().backward()
+    xt = torch.tensor(x, dtype=torch.float64).permute(0, 3, 1, 2)
+    gt = torch.tensor(g, dtype=torch.float64).permute(0, 3, 1, 2)
+    wshape = (co, ci, 3, 3)
+    ref_w = torch.nn.grad.conv2d_weight(xt, wshape, gt, padding=1)
+    S_w = torch.nn.grad.conv2d_weight(xt.abs(), wshape, gt.abs(), padding=1)
+    to_lib = lambda t: t.permute(2, 3, 0, 1).reshape(9, co, ci).numpy()   # [Cout][Cin][ky][kx] -> [tap][Cout][Cin]
     dw = torch.zeros((9, co, ci), dtype=torch.float32, device="cuda")
     gd = torch.tensor(g).to(torch.bfloat16).cuda()
     tv.lib().tvcut_conv3x3_wgrad_bf16(xd.data_ptr(), gd.data_ptr(), dw.data_ptr(), n, h, w, ci, co, None)
     torch.cuda.synchronize()
-    assert rel(dw.cpu().numpy(), W.grad.numpy()) < 2e-2
+    d = np.abs(dw.cpu().numpy().astype(np.float64) - to_lib(ref_w))
+    assert np.all(d <= 2 ** -12 * to_lib(S_w)), float((d / (2 ** -12 * to_lib(S_w) + 1e-300)).max())
 
 
 TC_SHAPES = [(1, 16, 128, 16, 32), (2, 16, 64, 32, 16), (1, 8, 256, 64, 128), (1, 4, 128, 128, 256),
@@ -68,7 +118,6 @@ def test_conv_tcgen05(tv, shape, relu):
     """The tcgen05 kernel (engine 2) against the CPU reference and against the
     mma.sync kernel (engine 1): same BF16 inputs, FP32 accumulation in a
     different order, so the BF16 outputs differ by rounding only."""
-    from oracle import unet_ref
     n, h, w, ci, co = shape
     rng = np.random.default_rng(sum(shape) + relu)
     x = bf16_round(rng.normal(size=(n, h, w, ci)))
@@ -90,14 +139,9 @@ def test_conv_tcgen05(tv, shape, relu):
     # MMAs in the same order
     np.testing.assert_array_equal(outs[0], outs[2])
     np.testing.assert_array_equal(outs[3], outs[2])
-    Wt = torch.tensor(wk).reshape(3, 3, co, ci).permute(2, 3, 0, 1)
-    xt = torch.tensor(x).permute(0, 3, 1, 2)
-    ref = unet_ref.F.conv2d(xt, Wt, torch.tensor(b), padding=1).permute(0, 2, 3, 1)
-    if relu:
-        ref = torch.relu(ref)
-    ref = ref.numpy()
-    assert rel(outs[0], ref) < 1e-2
-    assert rel(outs[0], outs[1]) < 1e-2
+    ref, S = conv_ref_and_scale(x, wk, b)
+    assert_conv_bound(outs[0], ref, S, relu=bool(relu))
+    assert_conv_bound(outs[1], ref, S, relu=bool(relu))
     # rounding only: no output differs by more than a few BF16 steps of its magnitude
     assert np.all(np.abs(outs[0] - outs[1]) <= 2 ** -6 * np.maximum(np.abs(outs[1]), 1.0))
 
@@ -178,60 +222,74 @@ def test_conv_tcgen05_rejects_other_shapes(tv):
     assert code == tv.OK
 
 
+def net_vs_oracle(tv, net, base, x, t, engine):
+    """GPU forward output, loss and parameter gradient of one engine, with
+    the BF16-storage oracle's on the GPU's own parameters."""
+    from oracle import unet_ref
+    net.set_engine(engine)
+    out = net.forward(torch.tensor(x).cuda()).cpu().numpy()
+    loss = net.backward(torch.tensor(t).cuda())
+    grad = net.params(which=1)
+    th = bf16_weights_f32_bias(net.params(), base)
+    ref_loss, ref_grad, ref_out = unet_ref.loss_and_grad(th, bf16_round(x), t, base, torch.float64, bf16_storage=True)
+    return out, loss, grad, ref_out, ref_loss, ref_grad
+
+
+def assert_forward_bound(out, ref_out):
+    scale = np.abs(ref_out).mean()
+    r = np.abs(out - ref_out) / (2 ** -8 * (np.abs(ref_out) + scale))
+    assert r.max() <= 8.0, float(r.max())
+
+
+def assert_gradient_bound(grad, ref_grad, base):
+    for li, sl in enumerate(layer_slices(base)):
+        g, ref = grad[sl], ref_grad[sl]
+        rms = np.sqrt(np.mean(ref ** 2))
+        r = np.abs(g - ref) / (2 ** -8 * (np.abs(ref) + rms))
+        assert r.max() <= 48.0, (li, float(r.max()))
+
+
 def test_network_engines_agree(tv):
     """128 x 128 images: every layer's shape goes to the tcgen05 kernel
-    (engine 0); the same network on the mma.sync kernels (engine 1) and the
-    CPU oracle agree with it."""
-    from oracle import unet_ref
+    (engine 0); the one-tile-per-CTA tcgen05 form (engine 3) gives the same
+    forward pass bit for bit, and every engine (also the mma.sync kernels,
+    engine 1) meets the element-wise bounds against the oracle."""
     base, n, h, w = 32, 2, 128, 128
     net = tv.UNet(base=base, batch=n, H=h, W=w, seed=5)
     rng = np.random.default_rng(6)
-    x = torch.tensor(rng.normal(size=(n, h, w, 3)).astype(np.float32)).cuda()
-    t = torch.tensor(rng.normal(size=(n, h, w, 2)).astype(np.float32)).cuda()
-    res = []
+    x = rng.normal(size=(n, h, w, 3)).astype(np.float32)
+    t = rng.normal(size=(n, h, w, 2)).astype(np.float32)
+    res = {}
     for engine in (0, 1, 3):
-        net.set_engine(engine)
-        out = net.forward(x).cpu().numpy()
-        loss = net.backward(t)
-        res.append((out, loss, net.params(which=1)))
+        out, loss, grad, ref_out, ref_loss, ref_grad = net_vs_oracle(tv, net, base, x, t, engine)
+        res[engine] = out
+        assert_forward_bound(out, ref_out)
+        assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+        assert_gradient_bound(grad, ref_grad, base)
     assert tv.lib().tvcut_conv_tc_error() == 0
-    np.testing.assert_array_equal(res[0][0], res[2][0])
-    # the weight gradient's kernel accumulates with atomics: equal up to summation order
-    assert rel(res[0][2], res[2][2]) < 1e-5
-    assert rel(res[0][0], res[1][0]) < 1e-2
-    assert abs(res[0][1] - res[1][1]) < 1e-2 * res[1][1]
-    assert rel(res[0][2], res[1][2]) < 5e-2
-    theta_bf = bf16_round(net.params())
-    ref_loss, _, ref_out = unet_ref.loss_and_grad(theta_bf, bf16_round(x.cpu().numpy()), t.cpu().numpy(), base)
-    assert rel(res[0][0], ref_out) < 5e-2
+    np.testing.assert_array_equal(res[0], res[3])
     net.close()
 
 
 def test_network_forward_backward(tv):
+    """A small, non-square image (levels down to 4 x 3 pixels): forward pass
+    and loss element by element; gradients of layers this small are sums
+    over a handful of pixels, so only their direction is compared here (the
+    element-wise gradient bounds are checked on 128 x 128 inputs above)."""
     from oracle import unet_ref
     base, n, h, w = 32, 2, 32, 24
     net = tv.UNet(base=base, batch=n, H=h, W=w, seed=7)
-    theta = net.params()
-    assert theta.size == unet_ref.num_params(base)
+    assert net.params().size == unet_ref.num_params(base)
     rng = np.random.default_rng(3)
     x = rng.normal(size=(n, h, w, 3)).astype(np.float32)
     t = rng.normal(size=(n, h, w, 2)).astype(np.float32)
-    out = net.forward(torch.tensor(x).cuda())
-    loss = net.backward(torch.tensor(t).cuda())
-    grad = net.params(which=1)
-    theta_bf = bf16_round(theta)                 # the forward pass uses BF16 weights
-    ref_loss, ref_grad, ref_out = unet_ref.loss_and_grad(theta_bf, bf16_round(x), t, base)
-    assert rel(out.cpu().numpy(), ref_out) < 5e-2
-    assert abs(loss - ref_loss) < 5e-2 * ref_loss
-    assert rel(grad, ref_grad) < 1e-1
-    # per-layer gradient direction
-    off = 0
-    for ci, co in unet_ref.layer_shapes(base):
-        k = 9 * ci * co + co
-        gl, rl = grad[off:off + k], ref_grad[off:off + k]
+    out, loss, grad, ref_out, ref_loss, ref_grad = net_vs_oracle(tv, net, base, x, t, 0)
+    assert_forward_bound(out, ref_out)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    for li, sl in enumerate(layer_slices(base)):
+        gl, rl = grad[sl], ref_grad[sl]
         cos = float(gl @ rl / (np.linalg.norm(gl) * np.linalg.norm(rl) + 1e-30))
-        assert cos > 0.98, (ci, co, cos)
-        off += k
+        assert cos > 0.98, (li, cos)
     net.close()
 
 

@@ -21,11 +21,11 @@ def tv():
     return tvcut
 
 
-def iters_to_cut(tv, s, e_star, z0=None, cap=3000):
-    if z0 is None:
+def iters_to_cut(tv, s, e_star, net=None, cap=3000):
+    if net is None:
         s.reset()
     else:
-        tv.tvcut_set_state(s.h, z0)
+        net.predict_state(s)
     for k in range(1, cap + 1):
         _, st = s.iterate(1)
         if st.energy_i64 == e_star:
@@ -55,10 +55,61 @@ def test_learned_warm_start_saves_iterations(tv, orc):
     s = tv.Solver((256, 256), dtype=tv.F32, check_every=1)
     s.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
     cold = iters_to_cut(tv, s, e_star)
-    warm = iters_to_cut(tv, s, e_star, learn.predict_state(net, w, a))
+    warm = iters_to_cut(tv, s, e_star, net)
     print(f"iterations to the exact min-cut: cold {cold}, learned warm start {warm}")
     assert warm <= 0.85 * cold, (cold, warm)
     lab, st = s.cut()
     assert st.energy_i64 == e_star and orc.energy(w, a, lab) == e_star
     net.close()
     s.close()
+
+
+@pytest.mark.parametrize("dims,algo", [((64, 96), 0), ((128, 40), 3), ((48, 48), 2)])
+def test_device_prediction_equals_host_features_path(tv, dims, algo):
+    """tvcut_unet_predict_state (features from the solver's device inputs,
+    forward pass, rescaling into the state's layouts) equals, bit for bit,
+    the same steps taken outside the library: host features, the FP32-input
+    forward pass, the FP32 rescaling and tvcut_set_state."""
+    from paper_1503_01563_gb300 import learn
+    w, a = inputs.uniform_grid(dims, 31)
+    net = tv.UNet(base=32, batch=1, H=dims[0], W=dims[1], seed=9)
+    s = tv.Solver(dims, algo=algo, dtype=tv.F32)
+    s.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
+    net.predict_state(s)
+    got = s.state()
+    f, sc = learn.features(w, a)
+    out = net.forward(torch.from_numpy(f[None]).cuda())
+    want = (out[0].permute(2, 0, 1) * sc).contiguous().cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert np.abs(want).max() > 0
+    # a handle on another stream: the prediction is ordered after its inputs
+    st = torch.cuda.Stream()
+    s2 = tv.Solver(dims, algo=algo, dtype=tv.F32, stream=st.cuda_stream)
+    s2.set_problem(torch.from_numpy(w).cuda(), [torch.from_numpy(x).cuda() for x in a])
+    net.predict_state(s2)
+    np.testing.assert_array_equal(s2.state(), want)
+    s.close()
+    s2.close()
+    net.close()
+
+
+def test_predict_state_rejects_other_grids(tv):
+    net = tv.UNet(base=16, batch=1, H=16, W=16, seed=1)
+    s3 = tv.Solver((8, 8, 8), dtype=tv.F32)
+    w, a = inputs.uniform_grid((8, 8, 8), 1)
+    s3.set_problem(w, a)
+    with pytest.raises(tv.TvcutError) as e:
+        net.predict_state(s3)
+    assert e.value.code == tv.ERR_INVALID
+    s2 = tv.Solver((12, 16), dtype=tv.F32)
+    with pytest.raises(tv.TvcutError) as e:
+        net.predict_state(s2)                            # inputs not set
+    assert e.value.code == tv.ERR_STATE
+    w, a = inputs.uniform_grid((12, 16), 1)
+    s2.set_problem(w, a)
+    with pytest.raises(tv.TvcutError) as e:
+        net.predict_state(s2)                            # 12 is not a multiple of 8
+    assert e.value.code == tv.ERR_INVALID
+    s2.close()
+    s3.close()
+    net.close()
