@@ -90,7 +90,11 @@ typedef struct {
                             a warp (speculative pieces, see csrc/scan.cu);
                             5: that schedule with thread-per-chain scans
                             forced; 6, 7, 8, 9: with 32, 16, 8 or 4 lanes per
-                            chain (speculative pieces) forced; 1, 2, 3: one fused
+                            chain (speculative pieces) forced; 10: the chain
+                            prox by parametric min-cuts with message passing
+                            (Sec. 3.2, "Message passing"), one CTA per chain
+                            of up to 2048 elements (longer chains as 5); 1, 2,
+                            3: one fused
                             sweep per block (prox and update in the same pass)
                             on shared-memory tiles of 8, 16, 32 chains; 4: the
                             fused sweeps with one thread per chain reading
@@ -436,6 +440,13 @@ tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h);
  * throughout; 3 is 0 with the one-tile-per-CTA tcgen05 kernel, 4 is 0
  * without the three-row form (the engines of tvcut_conv3x3_bf16_ex). */
 tvcut_status tvcut_unet_set_engine(tvcut_unet_t u, int engine);
+
+/* Diagnostic of mapping 10 (the message-passing chain prox): the number of
+ * chains, since the library was loaded or last reset, whose result failed
+ * the FP64 check of the chain prox's optimality conditions and was
+ * recomputed by the taut string.  *count receives it; reset != 0 sets it to
+ * 0.  Synchronises the device.  Errors: INVALID (NULL count), CUDA. */
+tvcut_status tvcut_mp_fallbacks(unsigned long long* count, int reset);
 
 /* Iterations without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot let a library allocate

@@ -152,7 +152,7 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
-    if (p->mapping < -1 || p->mapping > 9) { why = "params.mapping must be -1 (auto) or 0..9"; return false; }
+    if (p->mapping < -1 || p->mapping > 10) { why = "params.mapping must be -1 (auto) or 0..10"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
@@ -251,7 +251,8 @@ static T* S_of(tvcut_t h, int k) { return (T*)h->state + (int64_t)k * h->n; }
 template <typename T>
 static T* XK_of(tvcut_t h, int k) { return (T*)h->xk + (int64_t)k * h->n; }
 static int64_t cols_of(tvcut_t h) { return h->dims[h->ndim - 1]; }
-// mapping 5: thread per chain; 6, 7, 8, 9: 32, 16, 8, 4 lanes per chain
+// mapping 5: thread per chain; 6, 7, 8, 9: 32, 16, 8, 4 lanes per chain; 10:
+// the message-passing chain prox (mpprox.cu), a CTA per chain
 static int scan_force(int mapping) { return mapping >= 5 ? mapping - 4 : 0; }
 static int64_t rows_of(tvcut_t h) { return h->n / h->dims[h->ndim - 1]; }
 

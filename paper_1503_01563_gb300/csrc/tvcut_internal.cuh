@@ -198,6 +198,11 @@ cudaError_t launch_scan(ScanArgs<T> args, cudaStream_t s);
 // element, for every idx of a block stored as X describes (X.a compact).
 template <typename T>
 cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s);
+// Chain prox by parametric min-cuts with message passing (mpprox.cu): one CTA
+// per chain, chains of at most kMpMaxLen elements.
+constexpr int kMpMaxLen = 2048;
+template <typename T>
+cudaError_t launch_mp_prox(const ScanArgs<T>& A, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update(int mode, const UpdateArgs<T>& args, cudaStream_t s);
 template <typename T>

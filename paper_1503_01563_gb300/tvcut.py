@@ -35,7 +35,7 @@ EXPORTED = [
     "tvcut_unet_forward", "tvcut_unet_backward", "tvcut_unet_adam", "tvcut_unet_num_params",
     "tvcut_unet_get_params", "tvcut_unet_set_params", "tvcut_conv3x3_bf16", "tvcut_conv3x3_wgrad_bf16",
     "tvcut_conv3x3_bf16_ex", "tvcut_conv_tc_error", "tvcut_unet_set_engine", "tvcut_conv_tc_stall",
-    "tvcut_unet_predict_state",
+    "tvcut_unet_predict_state", "tvcut_mp_fallbacks",
 ]
 K_PROX, K_UPDATE, K_CHECK, K_OTHER, NKINDS = 0, 1, 2, 3, 4
 
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
         "tvcut_conv_tc_stall": (st, [c_int]),
         "tvcut_unet_set_engine": (st, [P, c_int]),
         "tvcut_unet_predict_state": (st, [P, P]),
+        "tvcut_mp_fallbacks": (st, [ctypes.POINTER(ctypes.c_ulonglong), c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,6 +279,14 @@ def tvcut_project_chains(dims, axis, v, a, out, what=0, stream=None):
         raise ValueError("tvcut_project_chains takes device tensors")
     s = ctypes.c_void_p(int(stream) if stream else 0)
     return _check(lib().tvcut_project_chains(len(dims), dims_arr, int(axis), pv, pa, po, dv, int(what), s))
+
+
+def tvcut_mp_fallbacks(reset=False):
+    """Chains of the message-passing prox (mapping 10) recomputed by the taut
+    string since the last reset."""
+    n = ctypes.c_ulonglong()
+    _check(lib().tvcut_mp_fallbacks(ctypes.byref(n), 1 if reset else 0))
+    return int(n.value)
 
 
 def tvcut_profile(h, enable: bool):
