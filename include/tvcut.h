@@ -371,7 +371,11 @@ tvcut_status tvcut_unet_resize(tvcut_unet_t u, int batch, int H, int W);
 /* in, out: DEVICE pointers; out may be NULL (keeps the result internal). */
 tvcut_status tvcut_unet_forward(tvcut_unet_t u, const float* in, float* out);
 /* After a forward: MSE loss against target (DEVICE, batch x H x W x 2),
- * parameter gradients (overwritten), loss to *loss (host, may be NULL). */
+ * parameter gradients (overwritten), loss to *loss (host, may be NULL).
+ * Deterministic: every reduction (weight and bias gradients, loss) sums its
+ * per-block partials in a fixed order, so equal inputs give equal bits and
+ * training from the same seed is reproducible.  The first call at a shape
+ * allocates the partials' scratch (a few MB). */
 tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target, float* loss);
 /* One Adam step on the FP32 master weights. */
 tvcut_status tvcut_unet_adam(tvcut_unet_t u, float lr, float beta1, float beta2, float eps);
@@ -381,7 +385,9 @@ tvcut_status tvcut_unet_get_params(tvcut_unet_t u, float* dst, int which);
 tvcut_status tvcut_unet_set_params(tvcut_unet_t u, const float* src);
 /* Single-layer kernels (DEVICE, BF16 as raw 16-bit words, NHWC, channels
  * multiples of 16): out = relu?(bias + conv3x3(in, wt)) with wt
- * [9][Cout][Cin]; dw[9][Cout][Cin] += sum_p dout[p][co] in[p + tap][ci]. */
+ * [9][Cout][Cin]; dw[9][Cout][Cin] += sum_p dout[p][co] in[p + tap][ci]
+ * (the single-layer weight gradient adds with atomics: its summation order,
+ * and so its last bits, may vary between calls). */
 tvcut_status tvcut_conv3x3_bf16(const void* in, const void* wt, const float* bias, void* out,
                                 int N, int H, int W, int Cin, int Cout, int relu,
                                 void* cuda_stream);

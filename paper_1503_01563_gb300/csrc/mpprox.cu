@@ -190,7 +190,6 @@ struct MpLayout {
     T* av;                  // a_i (edge i, i+1), 0 at the chain end
     T* xo;                  // final values
     T* sH;                  // per interval (indexed by its head): mean of v'
-    int* nH;                // per interval: element count
     int* hid;               // head index of each element's interval
     int* chg;               // per interval: splits + ties found this round
     unsigned char *act, *head, *hd, *tl;
@@ -199,50 +198,49 @@ struct MpLayout {
 };
 
 template <typename T>
-constexpr size_t mp_slot()                  // bytes per element of a scan buffer
+constexpr size_t mp_slot()                  // bytes per element of a scan buffer (maps, sums, FP64 check)
 {
-    return sizeof(ClampMap<T>) > sizeof(SumCount<double>) ? sizeof(ClampMap<T>) : sizeof(SumCount<double>);
+    return sizeof(ClampMap<T>) > sizeof(double) ? sizeof(ClampMap<T>) : sizeof(double);
 }
 
 template <typename T>
 constexpr size_t mp_part()                  // bytes of one scan Part (the largest value type)
 {
-    return sizeof(Part<ClampMap<T>>) > sizeof(Part<SumCount<double>>) ? sizeof(Part<ClampMap<T>>)
-                                                                       : sizeof(Part<SumCount<double>>);
+    return sizeof(Part<ClampMap<T>>) > sizeof(Part<double>) ? sizeof(Part<ClampMap<T>>) : sizeof(Part<double>);
 }
 
 // Byte offsets of the layout's sections, each rounded up to 16 bytes (the
-// scans keep doubles and 16-byte structs in them).  off[15] is the total.
+// scans keep doubles and 16-byte structs in them).  off[14] is the total.
 __host__ __device__ constexpr size_t mp_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 template <typename T>
 __host__ __device__ inline void mp_offsets(int M, size_t* off)
 {
-    const size_t sz[15] = {(size_t)M * mp_slot<T>(), (size_t)M * mp_slot<T>(), (size_t)M * sizeof(T),
+    const size_t sz[14] = {(size_t)M * mp_slot<T>(), (size_t)M * mp_slot<T>(), (size_t)M * sizeof(T),
                            (size_t)(kMpThreads + kMpWarps) * mp_part<T>(), (size_t)M * sizeof(T),
                            (size_t)M * sizeof(T), (size_t)M * sizeof(T), (size_t)M * sizeof(T),
-                           (size_t)M * sizeof(int), (size_t)M * sizeof(int), (size_t)M * sizeof(int),
-                           (size_t)M, (size_t)M, (size_t)M, (size_t)M};
+                           (size_t)M * sizeof(int), (size_t)M * sizeof(int), (size_t)M, (size_t)M, (size_t)M,
+                           (size_t)M};
     size_t o = 0;
-    for (int j = 0; j < 15; ++j) {
+    for (int j = 0; j < 14; ++j) {
         off[j] = o;
         o = mp_align16(o + sz[j]);
     }
-    off[15] = o + (size_t)M;                        // the class bytes last
+    off[14] = o + (size_t)M;                        // the class bytes last
 }
 
 template <typename T>
 inline size_t mp_smem_bytes(int M)
 {
-    size_t off[16];
+    size_t off[15];
     mp_offsets<T>(M, off);
-    return off[15];
+    return off[14];
 }
 
 template <typename T>
 __device__ MpLayout<T> mp_layout(unsigned char* base, int M)
 {
-    size_t off[16];
+    size_t off[15];
     mp_offsets<T>(M, off);
     MpLayout<T> L;
     L.fw = base + off[0];
@@ -253,14 +251,13 @@ __device__ MpLayout<T> mp_layout(unsigned char* base, int M)
     L.off = (T*)(base + off[5]);
     L.av = (T*)(base + off[6]);
     L.xo = (T*)(base + off[7]);
-    L.nH = (int*)(base + off[8]);
-    L.hid = (int*)(base + off[9]);
-    L.chg = (int*)(base + off[10]);
-    L.act = base + off[11];
-    L.head = base + off[12];
-    L.hd = base + off[13];
-    L.tl = base + off[14];
-    L.cls = (signed char*)(base + off[15] - (size_t)M);
+    L.hid = (int*)(base + off[8]);
+    L.chg = (int*)(base + off[9]);
+    L.act = base + off[10];
+    L.head = base + off[11];
+    L.hd = base + off[12];
+    L.tl = base + off[13];
+    L.cls = (signed char*)(base + off[14] - (size_t)M);
     return L;
 }
 
@@ -346,7 +343,6 @@ __global__ void __launch_bounds__(kMpThreads) mp_prox_kernel(ScanArgs<T> A, int 
             if (L.act[i] && L.tl[i]) {
                 const SumCount<T> sc = ((SumCount<T>*)L.fw)[i];
                 L.sH[h] = sc.s / (T)sc.n;                   // the interval's mean
-                L.nH[h] = sc.n;
             }
         }
         __syncthreads();

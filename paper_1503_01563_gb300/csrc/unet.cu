@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -237,8 +238,8 @@ __global__ void relu_mask_kernel(bf16* g, const bf16* y, int64_t n)
     }
 }
 
-// db[c] += sum_p g[p][c]
-__global__ void bias_grad_kernel(const bf16* g, float* db, int64_t P, int C)
+// part[block][c] = block's share of sum_p g[p][c]
+__global__ void bias_grad_kernel(const bf16* g, float* part, int64_t P, int C)
 {
     __shared__ float s[256];
     const int c = threadIdx.x % C;
@@ -252,11 +253,23 @@ __global__ void bias_grad_kernel(const bf16* g, float* db, int64_t P, int C)
     if (lane == 0) {
         float t = 0.f;
         for (int l = 0; l < lanes; ++l) t += s[l * C + c];
-        atomicAdd(&db[c], t);
+        part[(int64_t)blockIdx.x * C + c] = t;           // summed over the blocks in order afterwards
     }
 }
 
-// MSE over the first `used` of `C` output channels: loss partials, gradient 2 (o - t) / count
+// out[j] += sum_{c < nparts} part[c * n + j], in order of c (the deterministic
+// second stage of the gradient and loss reductions)
+__global__ void parts_reduce_kernel(const float* part, float* out, int64_t n, int nparts)
+{
+    GRID_STRIDE(j, n) {
+        float t = 0.f;
+        for (int c = 0; c < nparts; ++c) t += part[(int64_t)c * n + j];
+        out[j] += t;
+    }
+}
+
+// MSE over the first `used` of `C` output channels: loss partial per block (loss_acc[block]),
+// gradient 2 (o - t) / count
 __global__ void mse_kernel(const float* out, const float* target, bf16* gout, float* loss_acc, int64_t P, int C, int used,
                            float inv_count)
 {
@@ -273,7 +286,14 @@ __global__ void mse_kernel(const float* out, const float* target, bf16* gout, fl
         gout[i] = __float2bfloat16(g);
     }
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc * inv_count);
+    __shared__ float ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {                              // this block's share, summed in order afterwards
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        loss_acc[blockIdx.x] = t * inv_count;
+    }
 }
 
 __global__ void output_unpack_kernel(const float* o16, float* out, int64_t P, int C, int used)
@@ -338,6 +358,8 @@ struct tvcut_unet_ctx {
     std::vector<Act> acts;
     float* out16 = nullptr;                      // N x H x W x 16 FP32 output
     float* loss = nullptr;
+    float* gpart = nullptr;                      // partial sums of the gradient and loss reductions
+    int64_t gpart_cap = 0;                       // its size in floats (grown at a backward pass)
     int engine = 0;                              // convolutions: 0 tcgen05 where supported, 1 mma.sync
     std::string err;
 };
@@ -443,6 +465,7 @@ extern "C" void tvcut_unet_destroy(tvcut_unet_t u)
     cudaFree(u->wf);
     cudaFree(u->wd);
     cudaFree(u->loss);
+    cudaFree(u->gpart);
     delete u;
 }
 
@@ -661,6 +684,28 @@ extern "C" tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h)
     return TVCUT_OK;
 }
 
+// resolution level of each convolution's input, in forward order
+static const int kConvLevel[18] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0, 0};
+constexpr int64_t kWgradPixels = 4096;           // pixels per weight-gradient CTA
+constexpr int kBiasBlocks = 256;
+
+// Floats of partial sums the backward pass needs at the current shape: the
+// weight gradient's per-chunk slices of the largest layer, the bias
+// gradient's per-block rows, the loss's per-block values.
+static int64_t gpart_floats(tvcut_unet_t u)
+{
+    int64_t need = (int64_t)blocks_for((int64_t)u->N * u->H * u->W * 16);
+    for (size_t ci = 0; ci < u->convs.size(); ++ci) {
+        const Conv& c = u->convs[ci];
+        const int lv = kConvLevel[ci];
+        const int64_t P = (int64_t)u->N * (u->H >> lv) * (u->W >> lv);
+        const int64_t nch = (P + kWgradPixels - 1) / kWgradPixels;
+        if (nch > 1) need = std::max<int64_t>(need, nch * 9 * c.cin * c.cout);
+        need = std::max<int64_t>(need, (int64_t)kBiasBlocks * c.cout);
+    }
+    return need;
+}
+
 // gradient of conv ci: g_out is the gradient at its output (after the ReLU
 // mask); accumulates dW, db and writes the gradient of its input into gin
 // (overwrite) when gin != nullptr.
@@ -678,12 +723,16 @@ static tvcut_status conv_backward(tvcut_unet_t u, int ci, const Act& in, const A
     G.W = Wl;
     G.Cin = c.cin;
     G.Cout = c.cout;
-    G.pix_per_cta = 4096;
+    G.part = u->gpart;
+    G.pix_per_cta = kWgradPixels;
     const int nch = (int)((P + G.pix_per_cta - 1) / G.pix_per_cta);
     dim3 gw((unsigned)((c.cout + BM - 1) / BM), (unsigned)((c.cin + BN - 1) / BN), (unsigned)(9 * nch));
     conv3x3_wgrad_kernel<<<gw, 128, 0, u->stream>>>(G);
+    const int64_t nw = (int64_t)9 * c.cout * c.cin;
+    if (nch > 1) parts_reduce_kernel<<<blocks_for(nw), 256, 0, u->stream>>>(u->gpart, G.dw, nw, nch);
     const int lanes = 256 / c.cout > 0 ? 256 / c.cout : 1;
-    bias_grad_kernel<<<256, lanes * c.cout, 0, u->stream>>>(out.g, u->grads + c.boff, P, c.cout);
+    bias_grad_kernel<<<kBiasBlocks, lanes * c.cout, 0, u->stream>>>(out.g, u->gpart, P, c.cout);
+    parts_reduce_kernel<<<blocks_for(c.cout), 256, 0, u->stream>>>(u->gpart, u->grads + c.boff, c.cout, kBiasBlocks);
     if (gin) {
         ConvArgs A;
         A.in = out.g;
@@ -720,8 +769,19 @@ extern "C" tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target,
     const int64_t P0 = (int64_t)N * H * W;
     UCK(u, cudaMemsetAsync(u->grads, 0, sizeof(float) * (size_t)u->nparams, u->stream), "tvcut_unet_backward");
     UCK(u, cudaMemsetAsync(u->loss, 0, sizeof(float), u->stream), "tvcut_unet_backward");
-    mse_kernel<<<blocks_for(P0 * 16), 256, 0, u->stream>>>(u->out16, target, a[A_OUT].g, u->loss, P0, 16, 2,
-                                                           1.f / (float)(P0 * 2));
+    const int64_t need = gpart_floats(u);
+    if (u->gpart_cap < need) {
+        UCK(u, cudaStreamSynchronize(u->stream), "tvcut_unet_backward");
+        cudaFree(u->gpart);
+        u->gpart = nullptr;
+        u->gpart_cap = 0;
+        UCK(u, cudaMalloc(&u->gpart, sizeof(float) * (size_t)need), "tvcut_unet_backward: partial sums");
+        u->gpart_cap = need;
+    }
+    const int mblocks = blocks_for(P0 * 16);
+    mse_kernel<<<mblocks, 256, 0, u->stream>>>(u->out16, target, a[A_OUT].g, u->gpart, P0, 16, 2,
+                                               1.f / (float)(P0 * 2));
+    parts_reduce_kernel<<<1, 32, 0, u->stream>>>(u->gpart, u->loss, 1, mblocks);
     auto pool_b = [&](int o, int i) {       // a[i].g += pool'(a[o].g)
         const int lv = a[i].level;
         const int64_t n = (int64_t)N * (H >> lv) * (W >> lv) * a[i].c;
@@ -876,6 +936,7 @@ extern "C" tvcut_status tvcut_conv3x3_wgrad_bf16(const void* in, const void* dou
     G.in = (const bf16*)in;
     G.dout = (const bf16*)dout;
     G.dw = dw;
+    G.part = nullptr;                            // added atomically (summation order varies)
     G.N = N;
     G.H = H;
     G.W = W;

@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(FTHREADS) conv3x3_fwd_kernel(ConvArgs A)
 struct WgradArgs {
     const __nv_bfloat16* in;     // N x H x W x Cin   (layer input)
     const __nv_bfloat16* dout;   // N x H x W x Cout  (gradient of the layer output, after the ReLU mask)
-    float* dw;                   // 9 x Cout x Cin, accumulated (atomic)
+    float* dw;                   // 9 x Cout x Cin, accumulated
+    float* part;                 // nullptr: add into dw atomically; else one 9 x Cout x Cin slice per pixel
+                                 // chunk (written, not added), summed in chunk order afterwards
     int N, H, W, Cin, Cout;
     int64_t pix_per_cta;
 };
@@ -223,7 +225,11 @@ __global__ void __launch_bounds__(128) conv3x3_wgrad_kernel(WgradArgs A)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int ci = ci0 + nt * 8 + 2 * t + j;
-                if (ci < A.Cin) atomicAdd(&A.dw[((int64_t)k * A.Cout + co) * A.Cin + ci], acc[nt][2 * half + j]);
+                if (ci >= A.Cin) continue;
+                const int64_t idx = ((int64_t)k * A.Cout + co) * A.Cin + ci;
+                if (!A.part) atomicAdd(&A.dw[idx], acc[nt][2 * half + j]);
+                else if (nchunks == 1) A.dw[idx] += acc[nt][2 * half + j];      // the only writer of idx
+                else A.part[(int64_t)(blockIdx.z % nchunks) * 9 * A.Cout * A.Cin + idx] = acc[nt][2 * half + j];
             }
     }
 }

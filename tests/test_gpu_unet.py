@@ -293,6 +293,31 @@ def test_network_forward_backward(tv):
     net.close()
 
 
+def test_backward_and_training_are_deterministic(tv):
+    """Equal inputs give equal gradients bit for bit (the reductions sum
+    their partials in a fixed order), and a few Adam steps from the same seed
+    give equal parameters, at a shape whose layers split the weight gradient
+    into many pixel chunks."""
+    rng = np.random.default_rng(9)
+    x = torch.tensor(rng.normal(size=(4, 64, 64, 3)).astype(np.float32)).cuda()
+    t = torch.tensor(rng.normal(size=(4, 64, 64, 2)).astype(np.float32)).cuda()
+    runs = []
+    for rep in range(2):
+        net = tv.UNet(base=32, batch=4, H=64, W=64, seed=13)
+        losses = []
+        for step in range(3):
+            net.forward(x)
+            losses.append(net.backward(t))
+            if step == 0:
+                g0 = net.params(which=1)
+            net.adam(lr=1e-3)
+        runs.append((g0, losses, net.params()))
+        net.close()
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
 def test_training_reduces_loss(tv):
     net = tv.UNet(base=32, batch=4, H=32, W=32, seed=11)
     rng = np.random.default_rng(4)
