@@ -120,18 +120,21 @@ typedef struct {
                             (r, c+1)-(r+1, c), both (H-1) x (W-1) row-major.
                             8 needs ndim 2 and the scan schedule (mapping -1, 0
                             or 5..9); states then have 4*n values */
-    int certify;         /* 0 (default): evaluate the rigorous lower bound
-                            (stats.certified_lb) only when the approximate one
-                            is close to the energy and the iterate precision
-                            can certify the grid; 1: at every check (costs one
-                            projection scan and two passes over the grid) */
+    int certify;         /* when to evaluate the rigorous lower bound
+                            (stats.certified_lb) on integer data: 0 (default)
+                            for FP64 iterates when the approximate bound is
+                            within 1 + 1e-7 |energy| of the energy, never for
+                            FP32 iterates; 2: when close, for both (FP32
+                            iterates then get their block duals recomputed in
+                            FP64 from the FP32 state, about the cost of one
+                            FP64 iteration, and certify grids of 10^7
+                            vertices); 1: at every check */
     int stop_on_approx;  /* 1: tvcut_iterate also stops when energy -
                             discrete_lb < 1 on integer data, the certificate
                             evaluated with the iterate's own (approximate)
-                            dual.  Not a proof: it is the stop rule for FP32
-                            iterates on large grids, whose rigorous bound stays
-                            about 1e-4 |E| below the energy (FP32 rounding of
-                            the duals summed over the grid).  Default 0 */
+                            dual.  Not a proof, and no FP64 work: the cheap
+                            stop rule for FP32 iterates (certify 2 turns the
+                            same moment into a proof).  Default 0 */
     int reserved[4];     /* must be zero */
 } tvcut_params;
 
@@ -162,14 +165,13 @@ typedef struct {
                               chain by chain (running sums of each chain's dual
                               clamped to [-a, a]) and evaluated as
                               sum_i min(y_i - w_i, 0) in FP64, minus a bound on
-                              that sum's rounding.  Evaluated on integer data
-                              when params.certify is 1, or when
-                              energy - discrete_lb < 1 + 1e-7 |energy| and the
-                              iterate precision can close it (n * eps *
-                              max|x| < 1/2, eps = 2^-24 for FP32, 2^-53 for
-                              FP64: FP32 iterates cannot certify grids much
-                              beyond 10^5 vertices); -infinity when not
-                              evaluated */
+                              that sum's rounding.  With FP32 iterates the
+                              block duals are recomputed in FP64 from the FP32
+                              state first (AAR, AP: FP64 chain projections;
+                              BCD, FISTA: one FP64 block-coordinate sweep), as
+                              duals computed in FP32 leave the bound ~1e-5 |E|
+                              low on large grids.  When it is evaluated: see
+                              params.certify; -infinity when not evaluated */
     int64_t reserved[2];
 } tvcut_stats;
 

@@ -49,6 +49,10 @@ struct tvcut_ctx {
     bool tlast = true;             // scan schedule: block ndim-1 (state, weights) stored transposed
     uint8_t* labels = nullptr;     // n
     double* ycert = nullptr;       // n, FP64: the exactly feasible dual of the rigorous bound (on first use)
+    double* y64 = nullptr;         // FP32 iterates: nblk * n FP64 block duals for the bound (on first use)
+    double* a64 = nullptr;         // nblk * n: the blocks' weights in FP64
+    double* w64 = nullptr;         // n: the unary in FP64
+    double* t64 = nullptr;         // n: FP64 scratch
     double* lbpart = nullptr;      // 2 * kCheckBlocks partial sums of that bound
     CheckPartial* partials = nullptr;
     LevelPartial* level_partials = nullptr;
@@ -131,6 +135,10 @@ extern "C" void tvcut_destroy(tvcut_t h)
     cudaFree(h->labels);
     cudaFree(h->ycert);
     cudaFree(h->lbpart);
+    cudaFree(h->y64);
+    cudaFree(h->a64);
+    cudaFree(h->w64);
+    cudaFree(h->t64);
     cudaFree(h->partials);
     cudaFree(h->level_partials);
     cudaFree(h->dstatus);
@@ -156,7 +164,7 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }
-    if (p->certify != 0 && p->certify != 1) { why = "params.certify must be 0 or 1"; return false; }
+    if (p->certify < 0 || p->certify > 2) { why = "params.certify must be 0, 1 or 2"; return false; }
     if (p->stop_on_approx != 0 && p->stop_on_approx != 1) { why = "params.stop_on_approx must be 0 or 1"; return false; }
     for (int i = 0; i < 4; ++i) if (p->reserved[i]) { why = "params.reserved must be zero"; return false; }
     if (p->connectivity != 0 && p->connectivity != 4 && p->connectivity != 6 && p->connectivity != 8) {
@@ -665,6 +673,110 @@ static cudaError_t run_iteration(tvcut_t h, int mode, int check)
     return traced(h, TVCUT_K_UPDATE, 1, [&] { return launch_update<T>(mode, U, h->stream); });
 }
 
+// Block k's chain geometry over FP64 arrays (v, a compact, x), as block_axis.
+template <typename T>
+static ScanAxis<double> axis64(tvcut_t h, int k, const double* v, const double* a, double* x)
+{
+    const ScanAxis<T> G = block_axis<T>(h, k, nullptr, nullptr);
+    ScanAxis<double> X;
+    memset(&X, 0, sizeof(X));
+    X.nchains = G.nchains;
+    X.inner = G.inner;
+    X.m = G.m;
+    X.transposed = G.transposed;
+    X.v = v;
+    X.a = a;
+    X.ap = nullptr;
+    X.x = x;
+    return X;
+}
+
+// FP64 block duals of an FP32 handle's current state, for the rigorous bound.
+// The FP32 state is an exact input, but duals computed from it in FP32 carry
+// the chain prox's rounding at the state's magnitude (about eps |z| per
+// element), which the bound sums over the grid: on 256^3 it leaves the bound
+// ~10^3 below the energy.  So the duals are recomputed in FP64: for AAR and
+// AP the FP64 chain projections of the state blocks, for BCD and FISTA one
+// FP64 sweep of block coordinate descent (y_k <- Pi_{K_k}(w - sum_{j != k}
+// y_j), blocks in turn) from their FP32 duals.  Fills h->y64 and h->a64.
+template <typename T>
+static cudaError_t fp64_duals(tvcut_t h, int* nlaunch)
+{
+    const size_t nb = (size_t)h->nblk * (size_t)h->n;
+    cudaError_t e = cudaSuccess;
+    if (!h->y64) {
+        e = cudaMalloc(&h->y64, sizeof(double) * nb);
+        if (e == cudaSuccess) e = cudaMalloc(&h->a64, sizeof(double) * nb);
+        if (e == cudaSuccess) e = cudaMalloc(&h->w64, sizeof(double) * (size_t)h->n);
+        if (e == cudaSuccess) e = cudaMalloc(&h->t64, sizeof(double) * (size_t)h->n);
+        if (e != cudaSuccess) return e;
+    }
+    int* flags = &h->dstatus->flags;
+    unsigned* amax = &h->dstatus->absmax_bits;
+    int nl = 0;
+    for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+        const ScanAxis<T> G = block_axis<T>(h, k, nullptr, nullptr);
+        const int64_t cnt = G.nchains * (int64_t)(G.m - 1);
+        if (cnt > 0) {
+            e = launch_convert<double>(h->a[k], TVCUT_F32, h->a64 + (size_t)k * h->n, cnt, false, flags, amax, h->stream);
+            ++nl;
+        }
+    }
+    const bool shadow_of_state = h->p.algo == TVCUT_AAR || h->p.algo == TVCUT_AP;
+    if (shadow_of_state) {
+        for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+            e = launch_convert<double>(S_of<T>(h, k), TVCUT_F32, h->t64, h->n, false, flags, amax, h->stream);
+            ScanArgs<double> S;
+            memset(&S, 0, sizeof(S));
+            S.naxes = 1;
+            S.shadow = 1;
+            S.ax[0] = axis64<T>(h, k, h->t64, h->a64 + (size_t)k * h->n, h->y64 + (size_t)k * h->n);
+            if (e == cudaSuccess) e = launch_scan<double>(S, h->stream);
+            nl += 2;
+        }
+    } else {
+        for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+            e = launch_convert<double>(S_of<T>(h, k), TVCUT_F32, h->y64 + (size_t)k * h->n, h->n, false, flags, amax,
+                                       h->stream);
+            ++nl;
+        }
+        if (e == cudaSuccess) e = launch_convert<double>(h->w, TVCUT_F32, h->w64, h->n, false, flags, amax, h->stream);
+        ++nl;
+        for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+            if (h->conn8) {
+                Prep8Args<double> A;
+                memset(&A, 0, sizeof(A));
+                A.rows = h->dims[0];
+                A.cols = h->dims[1];
+                for (int j = 0; j < 4; ++j) A.y[j] = h->y64 + (size_t)j * h->n;
+                A.w = h->w64;
+                A.k = k;
+                A.out[k] = h->t64;
+                e = launch_prep8<double>(PREP8_BCD, A, h->stream);
+            } else {
+                UpdateArgs<double> U;
+                memset(&U, 0, sizeof(U));
+                U.rows = rows_of(h);
+                U.cols = cols_of(h);
+                U.r = h->ndim;
+                for (int j = 0; j < h->ndim; ++j) U.s[j] = h->y64 + (size_t)j * h->n;
+                U.w = h->w64;
+                U.xout = h->t64;                          // v_k, in block k's layout
+                e = launch_bcd_prepare<double>(U, k, h->stream);
+            }
+            ScanArgs<double> S;
+            memset(&S, 0, sizeof(S));
+            S.naxes = 1;
+            S.shadow = 1;                                 // y_k = v_k - prox(v_k)
+            S.ax[0] = axis64<T>(h, k, h->t64, h->a64 + (size_t)k * h->n, h->y64 + (size_t)k * h->n);
+            if (e == cudaSuccess) e = launch_scan<double>(S, h->stream);
+            nl += 2;
+        }
+    }
+    *nlaunch = nl;
+    return e;
+}
+
 // Rigorous discrete lower bound (Sec. 2.2): the block duals of the current
 // state (the state itself for BCD and FISTA, its chain projections
 // Pi_{K_k}(s_k) for AAR and AP) made exactly feasible chain by chain in FP64,
@@ -678,6 +790,27 @@ static tvcut_status rigorous_lb(tvcut_t h, double* lb_out)
         CK(h, cudaMalloc(&h->lbpart, sizeof(double) * 2 * kCheckBlocks), "certify: allocation");
     }
     const bool shadow = h->p.algo == TVCUT_AAR || h->p.algo == TVCUT_AP;
+    if (sizeof(T) == 4) {                                 // FP32 iterates: the duals in FP64
+        int nl = 0;
+        CK(h, fp64_duals<T>(h, &nl), "certify: FP64 duals");
+        h->launches[TVCUT_K_CHECK] += nl;
+        CK(h, traced(h, TVCUT_K_CHECK, h->nblk + 1, [&] {
+               cudaError_t e = cudaSuccess;
+               for (int k = 0; k < h->nblk && e == cudaSuccess; ++k) {
+                   CertifyArgs<double> A;
+                   memset(&A, 0, sizeof(A));
+                   A.X = axis64<T>(h, k, h->y64 + (size_t)k * h->n, h->a64 + (size_t)k * h->n, nullptr);
+                   A.layout = block_layout(h, k);
+                   A.first = k == 0 ? 1 : 0;
+                   A.H = h->dims[0];
+                   A.W = h->ndim == 2 ? h->dims[1] : 1;
+                   A.Y = h->ycert;
+                   e = launch_certify_block<double>(A, h->stream);
+               }
+               if (e == cudaSuccess) e = launch_certify_lb<T>(h->ycert, (const T*)h->w, h->n, h->lbpart, h->stream);
+               return e;
+           }), "certify");
+    } else {
     const T* yk[4];
     for (int k = 0; k < h->nblk; ++k) yk[k] = shadow ? XK_of<T>(h, k) : S_of<T>(h, k);
     const int nk = (shadow ? 1 : 0) + h->nblk + 1;
@@ -705,6 +838,7 @@ static tvcut_status rigorous_lb(tvcut_t h, double* lb_out)
            if (e == cudaSuccess) e = launch_certify_lb<T>(h->ycert, (const T*)h->w, h->n, h->lbpart, h->stream);
            return e;
        }), "certify");
+    }
     std::vector<double> part(2 * kCheckBlocks);
     CK(h, cudaMemcpyAsync(part.data(), h->lbpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream),
        "certify");
@@ -796,19 +930,21 @@ static tvcut_status run_check(tvcut_t h)
     st.tv_value = s.tv;
     st.tv_gap = s.tv - s.ytx;
     st.x_absmax = s.xabs;
-    // certified only against the rigorous bound; it is evaluated when asked
-    // for at every check, or when the approximate bound is within
-    // 1 + 1e-7 |E| of the energy and the iterate's precision can bring it
-    // within 1: its rounding floor n * eps * max|x| (the duals' rounding
-    // summed over the grid) must stay below 1/2
+    // certified only against the rigorous bound; it is evaluated at every
+    // check (certify 1), or when the approximate bound is within 1 + 1e-7 |E|
+    // of the energy and FP64 duals can bring it within 1 (their rounding
+    // floor n * 2^-53 * max|x| summed over the grid stays below 1/2): by
+    // default for FP64 iterates, with certify 2 also for FP32 ones, whose
+    // duals are then recomputed in FP64 (about one FP64 iteration)
     st.certified = 0;
     st.certified_lb = -INFINITY;
     h->labels_valid = true;
     if (exact) {
         const double E = (double)st.energy_i64;
-        const double eps = sizeof(T) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53);
-        const bool reachable = (double)h->n * eps * std::max(s.xabs, 1.0) < 0.5;
-        if (h->p.certify == 1 || (reachable && E - s.lb < 1.0 + 1e-7 * fabs(E))) {
+        const bool reachable = (double)h->n * ldexp(1.0, -53) * std::max(s.xabs, 1.0) < 0.5;   // FP64 duals
+        const bool close = reachable && E - s.lb < 1.0 + 1e-7 * fabs(E);
+        const bool when_close = h->p.certify == 2 || (h->p.certify == 0 && sizeof(T) == 8);
+        if (h->p.certify == 1 || (when_close && close)) {
             double lb = 0.0;
             tvcut_status cs = rigorous_lb<T>(h, &lb);
             if (cs != TVCUT_OK) return cs;

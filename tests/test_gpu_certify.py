@@ -101,3 +101,21 @@ def test_approximate_bound_can_exceed_min_cut(tv, orc):
     rows = run_checks(tv, w, a, 0, tv.F32, 500, 10)
     assert all(r[2] <= e_star for r in rows)
     assert max(r[3] for r in rows) > e_star
+
+
+@pytest.mark.parametrize("kind,dims,algo", [("vol", (96, 96, 96), 0), ("seg", (512, 512), 0), ("seg", (512, 512), 2),
+                                            ("vol", (64, 64, 64), 3)])
+def test_fp32_iterates_certify_with_fp64_duals(tv, orc, kind, dims, algo):
+    """FP32 iterates with params.certify = 2: once the approximate gap is
+    small, the block duals are recomputed in FP64 from the FP32 state, and the
+    solve stops with a proof: certified, the max-flow energy, the bound within
+    1 of it and never above it."""
+    w, a = inputs.volume_problem(dims, 9) if kind == "vol" else inputs.segmentation_problem(dims, 9)
+    e_star = orc.maxflow(w, a)[1]
+    s = tv.Solver(dims, algo=algo, dtype=tv.F32, check_every=5, certify=2)
+    s.set_problem(w, a)
+    code, st = s.iterate(3000)
+    assert code == tv.OK and st.certified, (st.iters, st.energy_i64 - st.certified_lb)
+    assert st.energy_i64 == e_star
+    assert e_star - 1 < st.certified_lb <= e_star
+    s.close()
