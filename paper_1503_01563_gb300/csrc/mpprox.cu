@@ -191,7 +191,7 @@ struct MpLayout {
     T* xo;                  // final values
     T* sH;                  // per interval (indexed by its head): mean of v'
     int* hid;               // head index of each element's interval
-    int* chg;               // per interval: splits + ties found this round
+    int* chg;               // per interval: splits + ties found in the current pass
     unsigned char *act, *head, *hd, *tl;
     signed char* cls;
     void* scratch;
