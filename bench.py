@@ -952,6 +952,24 @@ def run_ours(args):
             sv.close()
             methods[mname] = {"iters": km, "ms": float(np.median(times)), "energies_match": ok,
                               "Mvertex_iter_s": n * km / (float(np.median(times)) / 1e3) / 1e6}
+            if mname == "bcd":          # the same solve stopped by the library's certificate (FP64 duals)
+                sv = tvcut.Solver(dims, algo=mcode, dtype=tvcut.F32, check_every=2, certify=2,
+                                  stream=stream.cuda_stream)
+                sv.set_problem(wd, ad)
+                times, res = [], None
+                for rep in range(3):
+                    flush.zero_()
+                    ev0.record(stream)
+                    tvcut.tvcut_reset(sv.h)
+                    code, st = sv.iterate(cap)
+                    ev1.record(stream)
+                    ev1.synchronize()
+                    times.append(ev0.elapsed_time(ev1))
+                    res = st
+                sv.close()
+                methods[mname]["certified"] = {
+                    "ms": float(np.median(times)), "iters": int(res.iters), "certified": bool(res.certified),
+                    "energy_equals_oracle": bool(res.energy_i64 == e_star), "check_every": 2}
     warm = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar" and not args.no_warm:
         warm, _ = warm_vs_cold(args, ["aar", "bcd"], local, cpu_leg=False)

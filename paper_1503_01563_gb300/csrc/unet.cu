@@ -103,8 +103,9 @@ __global__ void state_from_output_kernel(const float* __restrict__ o16, int H, i
     }
 }
 
-// 2x2 average: out (H/2 x W/2) from in (H x W); one 8-channel group per thread
-__global__ void pool_fwd_kernel(const bf16* in, bf16* out, int N, int H, int W, int C)
+// 2x2 average: out (H/2 x W/2, C channels) from in (H x W, pixel stride Cs); one
+// 8-channel group per thread
+__global__ void pool_fwd_kernel(const bf16* in, bf16* out, int N, int H, int W, int C, int Cs)
 {
     const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
     const int64_t total = (int64_t)N * Ho * Wo * C8;
@@ -115,13 +116,13 @@ __global__ void pool_fwd_kernel(const bf16* in, bf16* out, int N, int H, int W, 
         const int64_t q = po / Wo;
         const int y = (int)(q % Ho);
         const int64_t n = q / Ho;
-        const int64_t b = ((n * H + 2 * y) * W + 2 * x) * C + 8 * g;
-        const int64_t rs = (int64_t)W * C;
+        const int64_t b = ((n * H + 2 * y) * W + 2 * x) * Cs + 8 * g;
+        const int64_t rs = (int64_t)W * Cs;
         float f0[8], f1[8], f2[8], f3[8], r[8];
         unpack8(*(const uint4*)(in + b), f0);
-        unpack8(*(const uint4*)(in + b + C), f1);
+        unpack8(*(const uint4*)(in + b + Cs), f1);
         unpack8(*(const uint4*)(in + b + rs), f2);
-        unpack8(*(const uint4*)(in + b + rs + C), f3);
+        unpack8(*(const uint4*)(in + b + rs + Cs), f3);
 #pragma unroll
         for (int k = 0; k < 8; ++k) r[k] = 0.25f * (f0[k] + f1[k] + f2[k] + f3[k]);
         *(uint4*)(out + po * C + 8 * g) = pack8(r);
@@ -190,17 +191,6 @@ __global__ void up_bwd_kernel(const bf16* gout, bf16* gin, int N, int H, int W, 
     }
 }
 
-// out = [a | b] along channels
-__global__ void concat_fwd_kernel(const bf16* a, const bf16* b, bf16* out, int64_t P, int Ca, int Cb)
-{
-    const int C8 = (Ca + Cb) / 8, A8 = Ca / 8;
-    GRID_STRIDE(i, P * C8) {
-        const int64_t p = i / C8;
-        const int g = (int)(i - p * C8);
-        *(uint4*)(out + 8 * i) = g < A8 ? *(const uint4*)(a + p * Ca + 8 * g)
-                                        : *(const uint4*)(b + p * Cb + 8 * (g - A8));
-    }
-}
 
 // ga = g[:, :Ca] (overwrite); gb += g[:, Ca:]
 __global__ void concat_bwd_kernel(const bf16* g, bf16* ga, bf16* gb, int64_t P, int Ca, int Cb)
@@ -225,12 +215,14 @@ __global__ void concat_bwd_kernel(const bf16* g, bf16* ga, bf16* gb, int64_t P, 
 }
 
 // g *= (y > 0): gradient at a ReLU output -> gradient at its input (n % 8 == 0)
-__global__ void relu_mask_kernel(bf16* g, const bf16* y, int64_t n)
+// g (C channels per pixel) is zeroed where y (the activation, pixel stride Cs) is not positive
+__global__ void relu_mask_kernel(bf16* g, const bf16* y, int64_t n, int C, int Cs)
 {
     GRID_STRIDE(i, n / 8) {
         float gv[8], yv[8];
-        unpack8(*(const uint4*)(g + 8 * i), gv);
-        unpack8(*(const uint4*)(y + 8 * i), yv);
+        const int64_t e = 8 * i, p = e / C;
+        unpack8(*(const uint4*)(g + e), gv);
+        unpack8(*(const uint4*)(y + p * Cs + (e - p * C)), yv);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
             if (!(yv[k] > 0.f)) gv[k] = 0.f;
@@ -342,6 +334,9 @@ struct Act {                // one activation tensor (and its gradient)
     int c, level;           // channels, resolution level (0 = full)
     bf16* y = nullptr;
     bf16* g = nullptr;
+    int ys = 0;             // channels between consecutive pixels of y (0: c)
+    int vof = -1;           // >= 0: y is the channel slice [voff, voff + c) of act vof's y (not owned)
+    int voff = 0;
 };
 
 }  // namespace
@@ -414,12 +409,20 @@ static void define_net(tvcut_unet_t u)
         u->acts[i].c = ch[i];
         u->acts[i].level = lv[i];
     }
+    // the decoder's concatenations [upsampled branch, skip] are not copied: both
+    // producing convolutions write into their channel slices of the buffer
+    const int views[6][3] = {{A_U3, A_C3, 0}, {A_E3, A_C3, 4 * C}, {A_U2, A_C2, 0},
+                             {A_E2, A_C2, 2 * C}, {A_U1, A_C1, 0}, {A_E1, A_C1, C}};
+    for (const auto& v : views) {
+        u->acts[v[0]].vof = v[1];
+        u->acts[v[0]].voff = v[2];
+    }
 }
 
 static void free_acts(tvcut_unet_t u)
 {
     for (auto& a : u->acts) {
-        cudaFree(a.y);
+        if (a.vof < 0) cudaFree(a.y);
         cudaFree(a.g);
         a.y = a.g = nullptr;
     }
@@ -437,8 +440,13 @@ static tvcut_status alloc_acts(tvcut_unet_t u, int N, int H, int W)
     u->W = W;
     for (auto& a : u->acts) {
         const int64_t P = (int64_t)N * (H >> a.level) * (W >> a.level);
-        UCK(u, cudaMalloc(&a.y, sizeof(bf16) * P * a.c), "tvcut_unet activations");
+        if (a.vof < 0) UCK(u, cudaMalloc(&a.y, sizeof(bf16) * P * a.c), "tvcut_unet activations");
         UCK(u, cudaMalloc(&a.g, sizeof(bf16) * P * a.c), "tvcut_unet activations");
+    }
+    for (auto& a : u->acts) {
+        if (a.vof < 0) continue;
+        a.y = u->acts[a.vof].y + a.voff;
+        a.ys = u->acts[a.vof].c;
     }
     UCK(u, cudaMalloc(&u->out16, sizeof(float) * (int64_t)N * H * W * 16), "tvcut_unet activations");
     return TVCUT_OK;
@@ -556,7 +564,7 @@ static tvcut_status run_conv(tvcut_unet_t u, int ci, const Act& in, Act& out, co
     A.in = in.y;
     A.wt = wt + c.woff;
     A.bias = bias ? u->params + c.boff : nullptr;
-    A.out = out.y;
+    A.out = out.y;                           // a channel slice of a concatenation for the skip and upsampled branches
     A.out_f32 = (ci == (int)u->convs.size() - 1) ? u->out16 : nullptr;
     A.mask = nullptr;
     A.N = u->N;
@@ -564,7 +572,7 @@ static tvcut_status run_conv(tvcut_unet_t u, int ci, const Act& in, Act& out, co
     A.W = u->W >> in.level;
     A.Cin = c.cin;
     A.Cout = c.cout;
-    A.CoutStride = c.cout;
+    A.CoutStride = out.ys ? out.ys : c.cout;
     A.relu = c.relu;
     UCK(u, launch_conv(A, u->engine, u->stream), "conv forward");
     return TVCUT_OK;
@@ -582,18 +590,15 @@ static tvcut_status forward(tvcut_unet_t u, const float* in)
     auto pool = [&](int i, int o) {
         const int lv = a[i].level;
         const int64_t n = (int64_t)N * (H >> (lv + 1)) * (W >> (lv + 1)) * a[i].c;
-        pool_fwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
+        pool_fwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c,
+                                                                  a[i].ys ? a[i].ys : a[i].c);
     };
     auto up = [&](int i, int o) {
         const int lv = a[o].level;
         const int64_t n = (int64_t)N * (H >> lv) * (W >> lv) * a[i].c;
         up_fwd_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a[i].y, a[o].y, N, H >> lv, W >> lv, a[i].c);
     };
-    auto cat = [&](int x, int s, int o) {
-        const int lv = a[o].level;
-        const int64_t P = (int64_t)N * (H >> lv) * (W >> lv);
-        concat_fwd_kernel<<<blocks_for(P * a[o].c / 8), 256, 0, u->stream>>>(a[x].y, a[s].y, a[o].y, P, a[x].c, a[s].c);
-    };
+
     UST(run_conv(u, 0, a[A_X], a[A_E1A], wf, true));
     UST(run_conv(u, 1, a[A_E1A], a[A_E1], wf, true));
     pool(A_E1, A_P1);
@@ -607,17 +612,14 @@ static tvcut_status forward(tvcut_unet_t u, const float* in)
     UST(run_conv(u, 7, a[A_E4A], a[A_E4], wf, true));
     up(A_E4, A_U3A);
     UST(run_conv(u, 8, a[A_U3A], a[A_U3], wf, true));
-    cat(A_U3, A_E3, A_C3);
     UST(run_conv(u, 9, a[A_C3], a[A_D3A], wf, true));
     UST(run_conv(u, 10, a[A_D3A], a[A_D3], wf, true));
     up(A_D3, A_U2A);
     UST(run_conv(u, 11, a[A_U2A], a[A_U2], wf, true));
-    cat(A_U2, A_E2, A_C2);
     UST(run_conv(u, 12, a[A_C2], a[A_D2A], wf, true));
     UST(run_conv(u, 13, a[A_D2A], a[A_D2], wf, true));
     up(A_D2, A_U1A);
     UST(run_conv(u, 14, a[A_U1A], a[A_U1], wf, true));
-    cat(A_U1, A_E1, A_C1);
     UST(run_conv(u, 15, a[A_C1], a[A_D1A], wf, true));
     UST(run_conv(u, 16, a[A_D1A], a[A_D1], wf, true));
     UST(run_conv(u, 17, a[A_D1], a[A_OUT], wf, true));
@@ -757,7 +759,7 @@ static tvcut_status conv_backward(tvcut_unet_t u, int ci, const Act& in, const A
 static void mask(tvcut_unet_t u, Act& a)
 {
     const int64_t n = (int64_t)u->N * (u->H >> a.level) * (u->W >> a.level) * a.c;
-    relu_mask_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a.g, a.y, n);
+    relu_mask_kernel<<<blocks_for(n / 8), 256, 0, u->stream>>>(a.g, a.y, n, a.c, a.ys ? a.ys : a.c);
 }
 
 extern "C" tvcut_status tvcut_unet_backward(tvcut_unet_t u, const float* target, float* loss_out)

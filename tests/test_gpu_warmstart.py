@@ -93,6 +93,23 @@ def test_device_prediction_equals_host_features_path(tv, dims, algo):
     net.close()
 
 
+def test_device_prediction_fp64_handle(tv):
+    """An FP64 solver gets the same prediction as an FP32 one, widened: the
+    features are the same FP32 values and the rescaled output is an FP32
+    product in both."""
+    w, a = inputs.uniform_grid((64, 40), 33)
+    net = tv.UNet(base=32, batch=1, H=64, W=40, seed=4)
+    got = []
+    for dt in (tv.F32, tv.F64):
+        s = tv.Solver((64, 40), dtype=dt)
+        s.set_problem(w, a)
+        net.predict_state(s)
+        got.append(s.state())
+        s.close()
+    np.testing.assert_array_equal(got[0].astype(np.float64), got[1])
+    net.close()
+
+
 def test_predict_state_rejects_other_grids(tv):
     net = tv.UNet(base=16, batch=1, H=16, W=16, seed=1)
     s3 = tv.Solver((8, 8, 8), dtype=tv.F32)
