@@ -734,6 +734,51 @@ def run_unet(args):
     return 0
 
 
+def time_to_cut(name, algo_name, steps, warmup, stream, flush, mapping=-1):
+    """Cold start to the oracle-equal cut on another workload (the same rules
+    as the main line: k* found untimed, L2 flushed before each timed solve,
+    CUDA events on the library's stream)."""
+    import torch
+    from paper_1503_01563_gb300 import tvcut
+    w, a = make_problem(name)
+    dims = tuple(w.shape)
+    n = int(np.prod(dims))
+    e_star, _ = exact_min_cut(w, a)
+    wd = torch.from_numpy(w).cuda()
+    ad = [torch.from_numpy(x).cuda() for x in a]
+    code = ALGOS[algo_name]
+    cap = WORKLOADS[name]["cap"]
+    pr = tvcut.Solver(dims, algo=code, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream, mapping=mapping)
+    pr.set_problem(wd, ad)
+    km = None
+    for k in range(1, cap + 1):
+        _, st = pr.iterate(1)
+        if st.energy_i64 == e_star:
+            km = k
+            break
+    pr.close()
+    if km is None:
+        return {"iters": None}
+    sv = tvcut.Solver(dims, algo=code, dtype=tvcut.F32, check_every=km, stream=stream.cuda_stream, mapping=mapping)
+    sv.set_problem(wd, ad)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times, ok = [], True
+    for rep in range(warmup + steps):
+        flush.zero_()
+        e0.record(stream)
+        tvcut.tvcut_reset(sv.h)
+        _, st = sv.iterate(km)
+        e1.record(stream)
+        e1.synchronize()
+        ok = ok and st.energy_i64 == e_star
+        if rep >= warmup:
+            times.append(e0.elapsed_time(e1))
+    sv.close()
+    ms = float(np.median(times))
+    return {"dims": list(dims), "iters": km, "ms": ms, "Mvertex_iter_s": n * km / (ms / 1e3) / 1e6,
+            "energies_match": ok, "oracle_min_cut": e_star, "mapping": mapping}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -970,6 +1015,14 @@ def run_ours(args):
                 methods[mname]["certified"] = {
                     "ms": float(np.median(times)), "iters": int(res.iters), "certified": bool(res.certified),
                     "energy_equals_oracle": bool(res.energy_i64 == e_star), "check_every": 2}
+    # the 2D segmentation (1024^2 blobs) on the same GPU, for the driver's record
+    seg = None
+    if rank == 0 and args.workload == "volume256" and args.algo == "aar":
+        seg = {"workload": "seg1024",
+               "aar": time_to_cut("seg1024", "aar", max(3, args.steps // 2), args.warmup, stream, flush),
+               "bcd": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream, flush),
+               "bcd_message_passing": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream,
+                                                  flush, mapping=10)}
     warm = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar" and not args.no_warm:
         warm, _ = warm_vs_cold(args, ["aar", "bcd"], local, cpu_leg=False)
@@ -993,6 +1046,7 @@ def run_ours(args):
             "iters_to_oracle_equal_cut": kstar, "oracle_min_cut": e_star,
             "time_to_cut_own_stop_ms": own,
             "time_to_oracle_equal_cut_other_methods": methods,
+            "seg1024_time_to_oracle_equal_cut": seg,
             "fp32_vs_fp64": drift,
             "warm_start_2048": warm,
             "step_energies_match": all(e == e_star for e in energies),

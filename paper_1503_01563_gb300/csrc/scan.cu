@@ -346,15 +346,6 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
     // one thread per chain unless the launch has too few chains to fill the
     // GPU, in which case long chains go to the lane-group scan (measured
     // on 256^3: 65,536 chains of 256 run faster as warps, 196,608 as threads)
-    // automatic: a projection-mode launch of one block of at most 4,096 chains of
-    // 512-2,048 elements (a BCD step on a 2D grid) goes to the message-passing
-    // prox: on the 1024^2 segmentation's BCD iterates, whose long plateaus
-    // lengthen the lane-group scan's serial path, it takes 0.55 against 0.75 ms
-    // per launch (AAR and FISTA iterates, and short chains, stay faster on the
-    // taut string)
-    if (A.force == 0 && A.shadow && A.naxes == 1 && A.ax[0].m >= 512 && A.ax[0].m <= kMpMaxLen &&
-        A.ax[0].nchains <= 4096)
-        A.force = 6;
     if (A.force == 6) {            // message passing for the chains that fit, one thread per chain for the rest
         ScanArgs<T> mp = A, rest = A;
         mp.naxes = rest.naxes = 0;
