@@ -704,13 +704,26 @@ static cudaError_t fp64_duals(tvcut_t h, int* nlaunch)
 {
     const size_t nb = (size_t)h->nblk * (size_t)h->n;
     cudaError_t e = cudaSuccess;
-    if (!h->y64) {
-        e = cudaMalloc(&h->y64, sizeof(double) * nb);
-        if (e == cudaSuccess) e = cudaMalloc(&h->a64, sizeof(double) * nb);
-        if (e == cudaSuccess) e = cudaMalloc(&h->w64, sizeof(double) * (size_t)h->n);
-        if (e == cudaSuccess) e = cudaMalloc(&h->t64, sizeof(double) * (size_t)h->n);
-        if (e != cudaSuccess) return e;
+    if (!h->y64) {                                        // all four or none
+        double *y = nullptr, *a = nullptr, *w = nullptr, *t = nullptr;
+        e = cudaMalloc(&y, sizeof(double) * nb);
+        if (e == cudaSuccess) e = cudaMalloc(&a, sizeof(double) * nb);
+        if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * (size_t)h->n);
+        if (e == cudaSuccess) e = cudaMalloc(&t, sizeof(double) * (size_t)h->n);
+        if (e != cudaSuccess) {
+            cudaFree(y);
+            cudaFree(a);
+            cudaFree(w);
+            cudaFree(t);
+            return e;
+        }
+        h->y64 = y;
+        h->a64 = a;
+        h->w64 = w;
+        h->t64 = t;
     }
+    // the conversions' validation flags and max|v| land in the status record's
+    // fields, which only input validation reads (after clearing them)
     int* flags = &h->dstatus->flags;
     unsigned* amax = &h->dstatus->absmax_bits;
     int nl = 0;
@@ -785,9 +798,17 @@ static cudaError_t fp64_duals(tvcut_t h, int* nlaunch)
 template <typename T>
 static tvcut_status rigorous_lb(tvcut_t h, double* lb_out)
 {
-    if (!h->ycert) {
-        CK(h, cudaMalloc(&h->ycert, sizeof(double) * (size_t)h->n), "certify: allocation");
-        CK(h, cudaMalloc(&h->lbpart, sizeof(double) * 2 * kCheckBlocks), "certify: allocation");
+    if (!h->ycert) {                                      // both or neither
+        double *y = nullptr, *p = nullptr;
+        cudaError_t e = cudaMalloc(&y, sizeof(double) * (size_t)h->n);
+        if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(double) * 2 * kCheckBlocks);
+        if (e != cudaSuccess) {
+            cudaFree(y);
+            cudaFree(p);
+            return cuda_fail(h, e, "certify: allocation");
+        }
+        h->ycert = y;
+        h->lbpart = p;
     }
     const bool shadow = h->p.algo == TVCUT_AAR || h->p.algo == TVCUT_AP;
     if (sizeof(T) == 4) {                                 // FP32 iterates: the duals in FP64

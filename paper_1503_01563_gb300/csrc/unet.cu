@@ -653,9 +653,14 @@ extern "C" tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h)
     if (u->N != 1 || u->H != (int)v.H || u->W != (int)v.W) UST(alloc_acts(u, 1, (int)v.H, (int)v.W));
     const int H = (int)v.H, W = (int)v.W;
     const int64_t P = (int64_t)H * W;
+    struct EventGuard {                          // destroyed on every return path
+        cudaEvent_t e = nullptr;
+        ~EventGuard() { if (e) cudaEventDestroy(e); }
+    } guard;
     cudaEvent_t ev = nullptr;
     if (u->stream != v.stream) {                 // the network's stream runs after the handle's
         UCK(u, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "tvcut_unet_predict_state");
+        guard.e = ev;
         UCK(u, cudaEventRecord(ev, v.stream), "tvcut_unet_predict_state");
         UCK(u, cudaStreamWaitEvent(u->stream, ev, 0), "tvcut_unet_predict_state");
     }
@@ -679,7 +684,6 @@ extern "C" tvcut_status tvcut_unet_predict_state(tvcut_unet_t u, tvcut_t h)
     if (ev) {                                    // and the handle's stream after the network's
         UCK(u, cudaEventRecord(ev, u->stream), "tvcut_unet_predict_state");
         UCK(u, cudaStreamWaitEvent(v.stream, ev, 0), "tvcut_unet_predict_state");
-        cudaEventDestroy(ev);
     }
     st = tvcut::state_written(h);
     if (st != TVCUT_OK) return ufail(u, st, "tvcut_unet_predict_state: " + std::string(tvcut_last_error(h)));

@@ -54,6 +54,13 @@ def test_host_only_calls(built):
     p.check_every = 0
     assert lib.tvcut_create(2, dims, ctypes.byref(p), None, ctypes.byref(h)) == tvcut.ERR_INVALID
     assert lib.tvcut_iterate(None, 1, None) == tvcut.ERR_INVALID
+    for field, bad in (("certify", 3), ("certify", -1), ("stop_on_approx", 2), ("mapping", 11)):
+        q = tvcut.tvcut_default_params()
+        setattr(q, field, bad)
+        assert lib.tvcut_create(2, dims, ctypes.byref(q), None, ctypes.byref(h)) == tvcut.ERR_INVALID, field
+        assert field.encode() in lib.tvcut_last_error(None)
+    assert lib.tvcut_mp_fallbacks(None, 0) == tvcut.ERR_INVALID
+    assert lib.tvcut_unet_predict_state(None, None) == tvcut.ERR_INVALID
 
 
 def test_no_oracle_in_product_path():
