@@ -324,6 +324,81 @@ def batch_problems(G, seed):
     return dims, [inputs.uniform_grid(d, 1000 * seed + g) for g, d in enumerate(dims)]
 
 
+def batch_measure(dims, probs, algo, steps, warmup, stream, e_star, sample, cap, local, dist=None):
+    """The batched solve of `probs` (one handle, graph-replayed iterations):
+    autotune, k* = the first multiple of 10 iterations at which every sampled
+    grid's cut equals its E* (when e_star is given), `steps` timed solves with
+    the L2 flushed before each, then the same grids solved one after another
+    with one handle each."""
+    import torch
+    from paper_1503_01563_gb300 import tvcut
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dev_probs = [(torch.from_numpy(w).to(dev), [torch.from_numpy(x).to(dev) for x in a]) for w, a in probs]
+    b = tvcut.Batch(dims, algo=algo, dtype=tvcut.F32, stream=stream.cuda_stream)
+    for g, (w, a) in enumerate(dev_probs):
+        b.set_problem(g, w, a)
+    b.reset()
+    b.iterate(2)
+    chosen = b.autotune()
+    kstar = None
+    if e_star is not None:
+        b.reset()
+        k = 0
+        while k < cap:
+            _, st = b.iterate(10)
+            k += 10
+            if all(st[g].energy_i64 == e_star[g] for g in sample):
+                kstar = k
+                break
+    iters = kstar if kstar else cap
+    if dist is not None:
+        t = torch.tensor([iters], device=dev)
+        dist.broadcast(t, 0)
+        iters = int(t.item())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        b.reset()
+        b.iterate(iters)
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, ok = 0.0, True
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        b.reset()
+        _, st = b.iterate(iters)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        if e_star is not None:
+            ok = ok and all(st[g].energy_i64 == e_star[g] for g in sample)
+    clk = clocks.stop()
+    singles = []
+    for g, (w, a) in enumerate(dev_probs):
+        sv = tvcut.Solver(dims[g], algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
+        sv.set_problem(w, a)
+        singles.append(sv)
+    for sv in singles[:8]:
+        sv.reset()
+        sv.iterate(iters)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for sv in singles:
+        sv.reset()
+        sv.iterate(iters)
+    ev1.record(stream)
+    ev1.synchronize()
+    sep_ms = ev0.elapsed_time(ev1)
+    for sv in singles:
+        sv.close()
+    b.close()
+    return {"kstar": kstar, "iters": iters, "total_ms": total_ms, "ok": ok, "clocks": clk, "chosen": chosen,
+            "sep_ms": sep_ms}
+
+
 def run_batch(args):
     """512 uneven 2D grids: one batched solve (graph-replayed iterations) vs
     the same grids solved one after another with one handle each.  --algo:
@@ -376,74 +451,16 @@ def run_batch(args):
     dev = torch.device("cuda", local)
     from paper_1503_01563_gb300 import tvcut
     stream = torch.cuda.current_stream(dev)
-    dev_probs = [(torch.from_numpy(w).to(dev), [torch.from_numpy(x).to(dev) for x in a]) for w, a in probs]
-    b = tvcut.Batch(dims, algo=algo, dtype=tvcut.F32, stream=stream.cuda_stream)
-    for g, (w, a) in enumerate(dev_probs):
-        b.set_problem(g, w, a)
-    b.reset()
-    b.iterate(2)
-    chosen = b.autotune()
-    # k*: first multiple of 10 iterations at which every sampled grid is at its E*
-    kstar = None
-    if rank == 0:
-        b.reset()
-        k = 0
-        while k < wl["cap"]:
-            _, st = b.iterate(10)
-            k += 10
-            if all(st[g].energy_i64 == e_star[g] for g in sample):
-                kstar = k
-                break
-    iters = kstar if kstar else wl["cap"]
-    if world > 1:
-        t = torch.tensor([iters], device=dev)
-        dist.broadcast(t, 0)
-        iters = int(t.item())
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        b.reset()
-        b.iterate(iters)
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    total_ms, ok = 0.0, True
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0.record(stream)
-        b.reset()
-        _, st = b.iterate(iters)
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-        ok = ok and all(st[g].energy_i64 == e_star.get(g, st[g].energy_i64) for g in sample)
-    clk = clocks.stop()
+    m = batch_measure(dims, probs, algo, args.steps, args.warmup, stream, e_star if rank == 0 else None, sample,
+                      wl["cap"], local, dist if world > 1 else None)
+    kstar, iters, total_ms, ok, clk, chosen, sep_ms = (m["kstar"], m["iters"], m["total_ms"], m["ok"], m["clocks"],
+                                                       m["chosen"], m["sep_ms"])
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = n_all * iters * args.steps / (total_ms / 1e3) / 1e6     # all ranks' grids / slowest rank
-    # the same grids solved one by one, one handle each
-    singles = []
-    for g, (w, a) in enumerate(dev_probs):
-        s = tvcut.Solver(dims[g], algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream)
-        s.set_problem(w, a)
-        singles.append(s)
-    for s in singles[:8]:
-        s.reset()
-        s.iterate(iters)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for s in singles:
-        s.reset()
-        s.iterate(iters)
-    ev1.record(stream)
-    ev1.synchronize()
-    sep_ms = ev0.elapsed_time(ev1)
-    for s in singles:
-        s.close()
     # end to end with host buffers: upload every grid, solve, read every labelling
     e2e_b = tvcut.Batch(dims, algo=algo, dtype=tvcut.F32, stream=stream.cuda_stream)
     pinned = [(torch.from_numpy(w).pin_memory(), [torch.from_numpy(x).pin_memory() for x in a]) for w, a in probs]
@@ -485,7 +502,6 @@ def run_batch(args):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n_total},
                "clocks": clk, "gpu_launches": (3 * iters + 4) if args.algo == "fista" else (2 * iters + 3)}
         print(json.dumps(out), flush=True)
-    b.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -1023,6 +1039,23 @@ def run_ours(args):
                "bcd": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream, flush),
                "bcd_message_passing": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream,
                                                   flush, mapping=10)}
+    # the batch of 512 uneven grids (AAR), for the driver's record
+    batch = None
+    if rank == 0 and args.workload == "volume256" and args.algo == "aar":
+        import oracle
+        oracle.build()
+        bwl = WORKLOADS["batch512"]
+        bdims, bprobs = batch_problems(bwl["grids"], bwl["seed"])
+        bsample = list(range(0, len(bdims), max(1, len(bdims) // 16)))
+        be = {g: oracle.maxflow(bprobs[g][0], bprobs[g][1], 1)[1] for g in bsample}
+        bn = int(sum(h * w for h, w in bdims))
+        bsteps = max(3, args.steps // 4)
+        m = batch_measure(bdims, bprobs, ALGOS["aar"], bsteps, 2, stream, be, bsample, bwl["cap"], local)
+        bms = m["total_ms"] / bsteps
+        batch = {"workload": "batch512", "grids": len(bdims), "vertices": bn, "iters": m["kstar"],
+                 "ms": bms if m["kstar"] else None, "Mvertex_iter_s": bn * m["iters"] / (bms / 1e3) / 1e6,
+                 "sampled_grids_match": m["ok"], "separate_solves_ms": m["sep_ms"],
+                 "speedup_of_batch": m["sep_ms"] / bms, "clocks": m["clocks"]}
     warm = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar" and not args.no_warm:
         warm, _ = warm_vs_cold(args, ["aar", "bcd"], local, cpu_leg=False)
@@ -1047,6 +1080,7 @@ def run_ours(args):
             "time_to_cut_own_stop_ms": own,
             "time_to_oracle_equal_cut_other_methods": methods,
             "seg1024_time_to_oracle_equal_cut": seg,
+            "batch512_time_to_oracle_equal_cut": batch,
             "fp32_vs_fp64": drift,
             "warm_start_2048": warm,
             "step_energies_match": all(e == e_star for e in energies),
