@@ -1058,7 +1058,7 @@ def run_ours(args):
                  "speedup_of_batch": m["sep_ms"] / bms, "clocks": m["clocks"]}
     warm = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar" and not args.no_warm:
-        warm, _ = warm_vs_cold(args, ["aar", "bcd"], local, cpu_leg=False)
+        warm, _ = warm_vs_cold(args, ["aar", "bcd", "fista"], local, cpu_leg=False)
 
     out = None
     if rank == 0:
@@ -1075,7 +1075,7 @@ def run_ours(args):
             "time_to_oracle_equal_cut_ms": {
                 "cold": ms_per_step if kstar else None, "warm": None,
                 "warm2048": None if warm is None else {
-                    k: warm[k]["ms"] for k in ("aar", "bcd")}},
+                    k: warm[k]["ms"] for k in ("aar", "bcd", "fista")}},
             "iters_to_oracle_equal_cut": kstar, "oracle_min_cut": e_star,
             "time_to_cut_own_stop_ms": own,
             "time_to_oracle_equal_cut_other_methods": methods,
