@@ -1038,7 +1038,10 @@ def run_ours(args):
                "aar": time_to_cut("seg1024", "aar", max(3, args.steps // 2), args.warmup, stream, flush),
                "bcd": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream, flush),
                "bcd_message_passing": time_to_cut("seg1024", "bcd", max(3, args.steps // 2), args.warmup, stream,
-                                                  flush, mapping=10)}
+                                                  flush, mapping=10),
+               "fista": time_to_cut("seg1024", "fista", max(3, args.steps // 2), args.warmup, stream, flush),
+               "fista_funnel": time_to_cut("seg1024", "fista", max(3, args.steps // 2), args.warmup, stream,
+                                           flush, mapping=11)}
     # the batch of 512 uneven grids (AAR), for the driver's record
     batch = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar":

@@ -93,7 +93,11 @@ typedef struct {
                             chain (speculative pieces) forced; 10: the chain
                             prox by parametric min-cuts with message passing
                             (Sec. 3.2, "Message passing"), one CTA per chain
-                            of up to 2048 elements (longer chains as 5); 1, 2,
+                            of up to 2048 elements (longer chains as 5); 11:
+                            the speculative pieces of 6..9 with the funnel
+                            form of the taut string (no restarts behind a
+                            bend, linear in the chain length), lanes per
+                            chain chosen as in the automatic rule; 1, 2,
                             3: one fused
                             sweep per block (prox and update in the same pass)
                             on shared-memory tiles of 8, 16, 32 chains; 4: the

@@ -28,6 +28,7 @@
 // scan writes the projection v - prox(v) directly (SHADOW).
 #include "tvcut_internal.cuh"
 #include "taut_string.cuh"
+#include "funnel.cuh"
 
 namespace tvcut {
 
@@ -120,14 +121,6 @@ cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s)
 // then exact, and lane L rewrites every position before it.  Lane 0 is
 // exact, so following merges from lane 0 reaches the chain end through
 // verified lanes only; lanes not on that path are overwritten.
-
-template <typename T>
-struct LaneState {
-    int s, i, ih, il;
-    T u0, th, tl, uh, ul, ah, al;
-};
-
-__host__ __device__ __forceinline__ int skew32(int j) { return j + (j >> 5); }
 
 // Advance one lane's scan through positions st.i .. stop-1 (data in shared
 // memory, skewed).  on_bend(s, e, d, t) is called for every finished segment
@@ -302,6 +295,235 @@ __global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
     }
 }
 
+// ---- lane-group scan with the funnel (no rescans) --------------------------
+//
+// The phases of wscan_kernel with the funnel form of the taut string
+// (funnel.cuh) in place of the local form: a lane's cost is then linear in
+// the elements it passes, where the local form restarts behind every bend
+// and is quadratic on the long plateaus of segmentation iterates.  Phase 2
+// keeps the segments of its continuation (up to kFunnelSegs), so that phase 3
+// writes them instead of scanning again.  A lane whose hull chain fills
+// (kFunnelQ vertices), or whose continuation has more segments, falls back to
+// the local form from its apex.
+
+constexpr int kFunnelQ = 16;
+constexpr int kFunnelSegs = 16;
+
+template <typename T>
+struct FSeg {
+    int e;
+    T t;
+};
+
+template <typename T, int G>
+__host__ __device__ __forceinline__ size_t fscan_lane_bytes()
+{
+    return (size_t)G * (2 * kFunnelQ * sizeof(FVert<T>) + kFunnelSegs * sizeof(FSeg<T>));
+}
+
+template <typename T, bool SHADOW, int G>
+__global__ void __launch_bounds__(256) fscan_kernel(ScanArgs<T> A, int nc)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    int k = 0;
+    while (k + 1 < A.naxes && blockIdx.x >= A.ax[k + 1].block_begin) ++k;
+    const ScanAxis<T>& X = A.ax[k];
+    const int m = X.m;
+    const int pitch = skew32(m) + 1;
+    FVert<T>* dq = (FVert<T>*)fsm;                                    // 2 rings per lane
+    FSeg<T>* sg = (FSeg<T>*)(dq + (size_t)nc * G * 2 * kFunnelQ);   // continuation segments per lane
+    T* sv = (T*)(sg + (size_t)nc * G * kFunnelSegs);
+    T* sa = sv + (size_t)nc * pitch;
+    uint8_t* code = (uint8_t*)(sa + (size_t)nc * pitch);
+    const int64_t c0 = (int64_t)(blockIdx.x - X.block_begin) * nc;
+    const int nvalid = (int)min((int64_t)nc, X.nchains - c0);
+
+    auto gbase = [&](int64_t c, int64_t& vb, int64_t& ab, int64_t& st) {
+        if (X.transposed) { vb = c; ab = c; st = X.nchains; }
+        else {
+            const int64_t o = c / X.inner, q = c - o * X.inner;
+            vb = o * (int64_t)m * X.inner + q;
+            ab = o * (int64_t)(m - 1) * X.inner + q;
+            st = X.inner;
+        }
+    };
+    for (int idx = threadIdx.x; idx < nc * m; idx += blockDim.x) {
+        const int c = idx % nc, j = idx / nc;
+        code[c * m + j] = 0;
+        if (c >= nvalid) continue;
+        int64_t vb, ab, st;
+        gbase(c0 + c, vb, ab, st);
+        scan_cp_elem(sv + c * pitch + skew32(j), X.v + vb + (int64_t)j * st);
+        if (j < m - 1) scan_cp_elem(sa + c * pitch + skew32(j), X.a + ab + (int64_t)j * st);
+    }
+    scan_cp_wait();
+    __syncthreads();
+
+    const int ch = threadIdx.x / G, gl = threadIdx.x % G;
+    const int glane0 = (threadIdx.x & 31) & ~(G - 1);
+    const bool valid = ch < nvalid;
+    int64_t vb = 0, ab = 0, gst = 0;
+    if (valid) gbase(c0 + ch, vb, ab, gst);
+    T* gx = X.x + vb;
+    const T* cv = sv + ch * pitch;
+    const T* ca = sa + ch * pitch;
+    uint8_t* cc = code + ch * m;
+    FVert<T>* U = dq + (size_t)threadIdx.x * 2 * kFunnelQ;
+    FVert<T>* L = U + kFunnelQ;
+    FSeg<T>* seg = sg + (size_t)threadIdx.x * kFunnelSegs;
+    const int lp = (m + G - 1) / G;
+    const int npieces = valid ? (m + lp - 1) / lp : 0;
+    const int p0 = gl * lp;
+    const int p1 = min(m, p0 + lp);
+    const bool active = gl < npieces;
+    const bool lastp = gl == npieces - 1;
+    auto write_seg = [&](int from, int to, T t) {
+        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = SHADOW ? cv[skew32(j)] - t : t;
+    };
+
+    // phase 1: every piece from a guessed state (a segment starting at the
+    // piece start with multiplier 0; exact for piece 0)
+    FunnelState<T> f = funnel_start<T>(p0);
+    LaneState<T> st{};
+    bool loc = false;                 // the lane runs the local form from here on
+    LaneState<T> open{};              // restart state of the open segment at the piece end
+    if (active) {
+        auto rec = [&](int s0, int e, int d, T t) {
+            if (d) cc[e] = (uint8_t)d;
+            write_seg(s0, e, t);
+            return false;
+        };
+        const int stop = lastp ? m : p1;
+        if (funnel_scan<T, kFunnelQ>(f, m, stop, cv, ca, U, L, rec) == 3) {
+            st = funnel_to_local<T>(f, ca);
+            loc = true;
+            lane_scan<T>(st, m, stop, cv, ca, rec);
+        }
+        if (loc) open = LaneState<T>{st.s, st.s, st.s, st.s, st.u0, T(0), T(0), T(0), T(0), T(0), T(0)};
+        else open = funnel_to_local<T>(f, ca);
+    }
+    __syncwarp();
+    // phase 2: continue until a bend recorded by a later piece (or the end),
+    // keeping the segments passed
+    int merge = m - 1, nseg = 0;
+    if (active && !lastp) {
+        auto keep = [&](int, int e, int d, T t) {
+            if (nseg < kFunnelSegs) seg[nseg] = FSeg<T>{e, t};
+            ++nseg;
+            if (d && e >= p1 && cc[e] == (uint8_t)d) {
+                merge = e;
+                return true;
+            }
+            return false;
+        };
+        if (!loc && funnel_scan<T, kFunnelQ>(f, m, m, cv, ca, U, L, keep) == 3) {
+            st = funnel_to_local<T>(f, ca);
+            loc = true;
+        }
+        if (loc) lane_scan<T>(st, m, m, cv, ca, keep);
+    }
+    const int target = (active && !lastp && merge < m - 1) ? merge / lp : npieces;
+    unsigned verified = 0;
+    int v = 0;
+#pragma unroll 1
+    for (int it = 0; it < G; ++it) {
+        const bool live = v < npieces;
+        if (live) verified |= 1u << v;
+        const int nv = __shfl_sync(0xffffffffu, target, glane0 + (live ? v : 0));
+        if (live) v = nv;
+    }
+    // phase 3: verified lanes write their continuation up to the merge bend
+    if (((verified >> gl) & 1u) && active && !lastp) {
+        if (nseg <= kFunnelSegs) {
+            int s0 = open.s;
+            for (int q = 0; q < nseg; ++q) {
+                const FSeg<T> sq = seg[q];
+                write_seg(s0, sq.e, sq.t);
+                s0 = sq.e + 1;
+            }
+        } else {
+            lane_scan<T>(open, m, m, cv, ca, [&](int s0, int e, int, T t) {
+                write_seg(s0, e, t);
+                return e >= merge;
+            });
+        }
+    }
+}
+
+template <typename T, int G>
+static size_t fscan_smem(int m, int nc)
+{
+    return (size_t)nc * (fscan_lane_bytes<T, G>() + 2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
+}
+
+// Chains per CTA for the funnel scan: whole warps, at most 256 threads, and
+// as many chains per SM as the shared memory allows (227 KB per SM).
+template <typename T, int G>
+static int fscan_chains(int m)
+{
+    const int per_warp = 32 / G;
+    int best = 0, best_per_sm = 0;
+    for (int nc = per_warp; nc * G <= 256; nc += per_warp) {
+        const size_t b = fscan_smem<T, G>(m, nc);
+        if (b > 227 * 1024) break;
+        const int per_sm = (int)((227 * 1024) / b) * nc;
+        if (per_sm > best_per_sm) { best = nc; best_per_sm = per_sm; }
+    }
+    return best;
+}
+
+template <typename T, bool SHADOW, int G>
+static cudaError_t launch_fscan_g(const ScanArgs<T>& wrp, int mmax, cudaStream_t s)
+{
+    const int nc = fscan_chains<T, G>(mmax);
+    if (nc == 0) return cudaErrorInvalidValue;
+    ScanArgs<T> a = wrp;
+    int64_t blocks = 0;
+    for (int k = 0; k < a.naxes; ++k) {
+        a.ax[k].block_begin = blocks;
+        blocks += (a.ax[k].nchains + nc - 1) / nc;
+    }
+    if (blocks == 0) return cudaSuccess;
+    const size_t smem = fscan_smem<T, G>(mmax, nc);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(fscan_kernel<T, SHADOW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    fscan_kernel<T, SHADOW, G><<<(unsigned)blocks, nc * G, smem, s>>>(a, nc);
+    return cudaGetLastError();
+}
+
+// Lanes per chain for the funnel scan: pieces of at least 16 elements, 4 to
+// 32 lanes, and fewer lanes when a chain's staging does not fit.
+template <typename T>
+static int fscan_lanes(int mmax)
+{
+    int G = 32;
+    while (G > 4 && mmax < 16 * G) G >>= 1;
+    auto fits = [&](int g) {
+        return g == 32 ? fscan_chains<T, 32>(mmax) > 0 : g == 16 ? fscan_chains<T, 16>(mmax) > 0
+             : g == 8 ? fscan_chains<T, 8>(mmax) > 0 : fscan_chains<T, 4>(mmax) > 0;
+    };
+    while (G > 4 && !fits(G)) G >>= 1;
+    return fits(G) ? G : 0;
+}
+
+template <typename T, bool SHADOW>
+static cudaError_t launch_fscan(const ScanArgs<T>& wrp, int G, int mmax, cudaStream_t s)
+{
+    switch (G) {
+    case 32: return launch_fscan_g<T, SHADOW, 32>(wrp, mmax, s);
+    case 16: return launch_fscan_g<T, SHADOW, 16>(wrp, mmax, s);
+    case 8: return launch_fscan_g<T, SHADOW, 8>(wrp, mmax, s);
+    default: return launch_fscan_g<T, SHADOW, 4>(wrp, mmax, s);
+    }
+}
+
 template <typename T>
 static size_t wscan_smem(int m, int nc)
 {
@@ -357,6 +579,26 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
         cudaError_t e = launch_mp_prox<T>(mp, s);
         if (e != cudaSuccess || rest.naxes == 0) return e;
         return launch_scan<T>(rest, s);
+    }
+    if (A.force == 7) {            // funnel lane groups for the chains whose staging fits, one thread per chain for the rest
+        ScanArgs<T> fun = A, rest = A;
+        fun.naxes = rest.naxes = 0;
+        rest.force = 1;
+        int mmax = 0;
+        for (int k = 0; k < A.naxes; ++k) {
+            if (A.ax[k].m >= 2 && fscan_lanes<T>(A.ax[k].m) > 0) {
+                fun.ax[fun.naxes++] = A.ax[k];
+                mmax = max(mmax, A.ax[k].m);
+            } else {
+                rest.ax[rest.naxes++] = A.ax[k];
+            }
+        }
+        if (fun.naxes) {
+            const int G = fscan_lanes<T>(mmax);
+            cudaError_t e = A.shadow ? launch_fscan<T, true>(fun, G, mmax, s) : launch_fscan<T, false>(fun, G, mmax, s);
+            if (e != cudaSuccess) return e;
+        }
+        return rest.naxes ? launch_scan<T>(rest, s) : cudaSuccess;
     }
     int64_t total = 0;
     for (int k = 0; k < A.naxes; ++k) total += A.ax[k].nchains;

@@ -6,6 +6,19 @@
 
 namespace tvcut {
 
+// A lane's local-form scan state (scan_chain's variables): segment start s,
+// next element i, the points ih/il that last limited th/tl, the incoming
+// multiplier u0 and the weights ah/al at ih/il.
+template <typename T>
+struct LaneState {
+    int s, i, ih, il;
+    T u0, th, tl, uh, ul, ah, al;
+};
+
+// Shared-memory index of element j of a staged chain (one pad word per 32,
+// so that lanes reading consecutive pieces hit different banks).
+__host__ __device__ __forceinline__ int skew32(int j) { return j + (j >> 5); }
+
 // Taut-string scan of one chain: element j of v at v[j*stride], weight of
 // edge (j, j+1) at a[j*stride]; writes x[j*stride] = prox value.  From a
 // segment start s with incoming multiplier u0, a common value t on s..i gives

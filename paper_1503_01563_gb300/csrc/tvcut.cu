@@ -160,7 +160,7 @@ static bool valid_params(const tvcut_params* p, std::string& why)
     }
     if (p->iterate_dtype != TVCUT_F32 && p->iterate_dtype != TVCUT_F64) { why = "params.iterate_dtype must be TVCUT_F32 or TVCUT_F64"; return false; }
     if (p->check_every < 1) { why = "params.check_every must be >= 1"; return false; }
-    if (p->mapping < -1 || p->mapping > 10) { why = "params.mapping must be -1 (auto) or 0..10"; return false; }
+    if (p->mapping < -1 || p->mapping > 11) { why = "params.mapping must be -1 (auto) or 0..11"; return false; }
     if (!(p->gap_tol >= 0.0)) { why = "params.gap_tol must be >= 0"; return false; }
     if (p->threshold != p->threshold) { why = "params.threshold is NaN"; return false; }
     if (p->level_sets < 0 || 2 * p->level_sets + 1 > kMaxLevels) { why = "params.level_sets must be in [0, 8]"; return false; }

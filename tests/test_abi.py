@@ -54,7 +54,7 @@ def test_host_only_calls(built):
     p.check_every = 0
     assert lib.tvcut_create(2, dims, ctypes.byref(p), None, ctypes.byref(h)) == tvcut.ERR_INVALID
     assert lib.tvcut_iterate(None, 1, None) == tvcut.ERR_INVALID
-    for field, bad in (("certify", 3), ("certify", -1), ("stop_on_approx", 2), ("mapping", 11)):
+    for field, bad in (("certify", 3), ("certify", -1), ("stop_on_approx", 2), ("mapping", 12)):
         q = tvcut.tvcut_default_params()
         setattr(q, field, bad)
         assert lib.tvcut_create(2, dims, ctypes.byref(q), None, ctypes.byref(h)) == tvcut.ERR_INVALID, field

@@ -31,7 +31,7 @@ def rel_err(got, want):
 
 
 @pytest.mark.parametrize("dims", CASES)
-@pytest.mark.parametrize("mapping", [-1, 5, 6, 8, 9])
+@pytest.mark.parametrize("mapping", [-1, 5, 6, 8, 9, 11])
 def test_bcd_iterations_f64(tv, orc, dims, mapping):
     w, a = inputs.uniform_grid(dims, 21)
     s = tv.Solver(dims, algo=BCD, dtype=tv.F64, check_every=1000, mapping=mapping)

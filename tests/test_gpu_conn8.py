@@ -35,7 +35,7 @@ def rel_err(got, want):
 
 @pytest.mark.parametrize("dims", CASES)
 @pytest.mark.parametrize("algo", [0, 1, 2, 3])
-@pytest.mark.parametrize("mapping", [-1, 5, 6, 8])
+@pytest.mark.parametrize("mapping", [-1, 5, 6, 8, 11])
 def test_conn8_iterations_f64(tv, c8, dims, algo, mapping):
     w, a = inputs.uniform_grid8(dims, 41)
     s = tv.Solver(dims, algo=algo, dtype=tv.F64, check_every=1000, mapping=mapping, connectivity=8)

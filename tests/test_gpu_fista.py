@@ -33,7 +33,7 @@ def rel_err(got, want):
 
 
 @pytest.mark.parametrize("dims", CASES)
-@pytest.mark.parametrize("mapping", [-1, 5, 6, 8, 9])
+@pytest.mark.parametrize("mapping", [-1, 5, 6, 8, 9, 11])
 def test_fista_iterations_f64(tv, orc, dims, mapping):
     w, a = inputs.uniform_grid(dims, 31)
     s = tv.Solver(dims, algo=FISTA, dtype=tv.F64, check_every=1000, mapping=mapping)

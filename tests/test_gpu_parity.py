@@ -99,7 +99,7 @@ ITER_CASES = [(64, 64), (37, 53), (1, 9), (9, 1), (2, 2), (13, 17, 19), (1, 5, 6
 
 @pytest.mark.parametrize("dims", ITER_CASES)
 @pytest.mark.parametrize("algo", [0, 1])
-@pytest.mark.parametrize("mapping", [-1, 1, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("mapping", [-1, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 def test_iterations_f64(tv, orc, dims, algo, mapping):
     w, a = inputs.uniform_grid(dims, 11)
     k = 17
