@@ -647,6 +647,53 @@ def run_warm(args):
     return 0
 
 
+def unet_layer_times(H, W, steps, warmup, only=None):
+    """Each of the U-Net's 18 convolutions alone at its shape in the forward
+    pass (batch 1, random BF16 input and weights, ReLU and bias, the default
+    engine), L2 flushed before each launch, CUDA events; with its floor: the
+    tensor peak for its flops or HBM for its BF16 input read once and output
+    written once, whichever is slower."""
+    import torch
+    from paper_1503_01563_gb300 import tvcut
+    lib = tvcut.lib()
+    hbm, _ = peaks()
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    tc = float(json.load(open(p))["bf16_tflops"]) if os.path.exists(p) else 1900.0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    rows = []
+    for li, (lvl, ci, co) in enumerate(UNET_CONVS):
+        if only is not None and li != only:
+            continue
+        h, w = H >> lvl, W >> lvl
+        x = torch.randn((1, h, w, ci), device="cuda", generator=g).to(torch.bfloat16)
+        wt = (torch.randn((9, co, ci), device="cuda", generator=g) * 0.05).to(torch.bfloat16)
+        b = torch.randn((co,), device="cuda", generator=g)
+        y = torch.empty((1, h, w, co), device="cuda", dtype=torch.bfloat16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for rep in range(warmup + steps):
+            flush.zero_()
+            e0.record()
+            code = lib.tvcut_conv3x3_bf16_ex(x.data_ptr(), wt.data_ptr(), b.data_ptr(), y.data_ptr(), 1, h, w, ci, co,
+                                             1, 0, None)
+            e1.record()
+            e1.synchronize()
+            if code != 0:
+                raise RuntimeError(f"tvcut_conv3x3_bf16_ex failed with status {code}")
+            if rep >= warmup:
+                ts.append(e0.elapsed_time(e1) * 1e3)
+        t_us = float(np.median(ts))
+        flops = 2.0 * h * w * 9 * ci * co
+        byts = h * w * (ci + co) * 2.0
+        floor_us = max(flops / (tc * 1e12), byts / (hbm * 1e9)) * 1e6
+        rows.append({"layer": li, "hw": h, "cin": ci, "cout": co, "us": t_us, "floor_us": floor_us,
+                     "bound": "hbm" if byts / (hbm * 1e9) > flops / (tc * 1e12) else "tensor",
+                     "frac_of_floor": floor_us / t_us})
+    return rows
+
+
 def run_unet(args):
     """U-Net inference at 2048^2: TFLOP/s of the forward pass (its 18 3x3
     convolutions as implicit GEMMs; pooling, upsampling and concatenation
@@ -661,6 +708,10 @@ def run_unet(args):
     from paper_1503_01563_gb300 import tvcut
     wl = WORKLOADS["unet2048"]
     H = W = args.unet_hw
+    if args.unet_layer >= 0:                       # one convolution alone (for profiling)
+        rows = unet_layer_times(H, W, args.steps, args.warmup, only=args.unet_layer)
+        print(json.dumps({"workload": f"unet{H} layer {args.unet_layer}", "per_layer": rows}), flush=True)
+        return 0
     flops = sum(2.0 * (H >> l) * (W >> l) * 9 * ci * co for l, ci, co in UNET_CONVS)
     g = np.random.default_rng(wl["seed"])
     x = g.normal(size=(1, H, W, 3)).astype(np.float32)
@@ -692,6 +743,7 @@ def run_unet(args):
             clk = clocks.stop()
         res[engine] = tot / args.steps
     err = tvcut.lib().tvcut_conv_tc_error()
+    per_layer = unet_layer_times(H, W, max(3, args.steps), args.warmup)
     # end to end: pinned host input -> forward -> host output
     xp = torch.from_numpy(x).pin_memory()
     op = torch.empty((1, H, W, 2), dtype=torch.float32).pin_memory()
@@ -739,6 +791,8 @@ def run_unet(args):
                              "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                              "peak_source": peak_kind, "traffic": None,
                              "layer_floor_ms": floor_s * 1e3, "frac_of_layer_floor": floor_s * 1e3 / res[0]},
+                "per_layer": {"layers": per_layer, "sum_us": sum(r["us"] for r in per_layer),
+                              "floor_sum_us": sum(r["floor_us"] for r in per_layer)},
                 "cpu_baseline": {"value": cpu_flops / t_cpu / 1e12, "unit": "TFLOP/s",
                                  "cores": torch.get_num_threads(), "kind": "oracle",
                                  "sample": f"oracle forward (PyTorch CPU FP32) on a {hs}x{hs} crop ({t_cpu:.2f} s)"},
@@ -829,7 +883,7 @@ def run_ours(args):
     cap = WORKLOADS[args.workload]["cap"]
     if rank == 0:
         probe = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=1, stream=stream.cuda_stream,
-                             connectivity=conn)
+                             mapping=args.mapping, connectivity=conn)
         probe.set_problem(wd, ad)
         for k in range(1, cap + 1):
             _, st = probe.iterate(1)
@@ -845,7 +899,7 @@ def run_ours(args):
         xs, cpu_base = cpu_leg(args.workload, w, a, kstar, budget_s=args.cpu_budget, algo=args.algo, t_mf=t_mf)
         if xs:
             chk = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=10 ** 6, stream=stream.cuda_stream,
-                               connectivity=conn)
+                               mapping=args.mapping, connectivity=conn)
             chk.set_problem(wd, ad)
             drift, done = {}, 0
             for k in sorted(xs):
@@ -863,7 +917,7 @@ def run_ours(args):
         iters = int(t.item())
 
     solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream,
-                          connectivity=conn)
+                          mapping=args.mapping, connectivity=conn)
     solver.set_problem(wd, ad)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -916,7 +970,8 @@ def run_ours(args):
     avg_s = kms[dom] / 1e3 / max(launches, 1)
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_kind = peaks()
-    traffic = kernel_traffic(dom_name, args.workload if args.algo == "aar" else f"{args.workload}:{args.algo}")
+    traffic = None if args.mapping != -1 else kernel_traffic(
+        dom_name, args.workload if args.algo == "aar" else f"{args.workload}:{args.algo}")
     moved = kind_bytes[0] + kind_bytes[1]
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
@@ -926,7 +981,7 @@ def run_ours(args):
 
     # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
     e2e_solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream,
-                              connectivity=conn)
+                              mapping=args.mapping, connectivity=conn)
     labels = torch.empty(dims, dtype=torch.uint8).pin_memory()
     w_pin = torch.from_numpy(w).pin_memory()
     a_pin = [torch.from_numpy(x).pin_memory() for x in a]
@@ -1071,7 +1126,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "dims": list(dims), "algo": args.algo.upper(), "iterate": "f32",
-                       "connectivity": conn if conn else 2 * len(dims), "blocks": ndim,
+                       "connectivity": conn if conn else 2 * len(dims), "blocks": ndim, "mapping": args.mapping,
                        "iters_per_step": iters, "step": "cold start + iterations to the oracle-equal cut + cut",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MB buffer written between steps"},
@@ -1113,8 +1168,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-warm", action="store_true",
                     help="skip the 2048^2 warm-vs-cold pair that the default volume256 line carries")
+    ap.add_argument("--unet-layer", type=int, default=-1,
+                    help="unet2048 workload: time one convolution of the network alone (0..17) and nothing else")
     ap.add_argument("--unet-hw", type=int, default=2048,
                     help="image size of the unet2048 workload (a multiple of 128; smaller for profiling)")
+    ap.add_argument("--mapping", type=int, default=-1,
+                    help="scan mapping of the timed solve (tvcut_params.mapping; -1 automatic, 10 message "
+                         "passing, 11 funnel taut string)")
     ap.add_argument("--algo", choices=sorted(ALGOS), default="aar",
                     help="iteration of the volume256/seg1024 workloads: AAR (Eq. 3), AP (Sec. 4.2), BCD or FISTA (Sec. 4.1)")
     args = ap.parse_args()
