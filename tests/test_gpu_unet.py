@@ -109,7 +109,9 @@ def test_conv_forward_and_wgrad(tv, shape):
 
 
 TC_SHAPES = [(1, 16, 128, 16, 32), (2, 16, 64, 32, 16), (1, 8, 256, 64, 128), (1, 4, 128, 128, 256),
-             (1, 16, 32, 256, 64), (3, 2, 128, 16, 16), (1, 64, 16, 64, 48)]
+             (1, 16, 32, 256, 64), (3, 2, 128, 16, 16), (1, 64, 16, 64, 48),
+             # halo strips: heights that are not a multiple of the strip, several images, 64 input channels
+             (2, 7, 128, 64, 32), (1, 5, 256, 32, 64), (3, 1, 128, 32, 32)]
 
 
 @pytest.mark.parametrize("shape", TC_SHAPES)
@@ -148,7 +150,9 @@ def test_conv_tcgen05(tv, shape, relu):
 
 @pytest.mark.parametrize("shape", [(1, 512, 512, 16, 32), (2, 256, 256, 64, 256), (4, 64, 128, 32, 64),
                                    (1, 1024, 64, 128, 128), (3, 96, 256, 256, 16), (1, 256, 256, 64, 32),
-                                   (2, 64, 384, 32, 48), (1, 128, 128, 16, 16)])
+                                   (2, 64, 384, 32, 48), (1, 128, 128, 16, 16),
+                                   (2, 131, 256, 64, 32), (3, 37, 384, 32, 32), (1, 258, 128, 16, 32),
+                                   (2, 2, 512, 32, 16)])
 def test_conv_tcgen05_persistent_many_tiles(tv, shape):
     """Shapes with several tiles per persistent CTA, so that both tensor-memory
     accumulator buffers and the stage or halo ring are reused many times: the
