@@ -978,6 +978,18 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
                 "share_of_step": float(kms[dom] / max(kms.sum(), 1e-9)),
                 "iteration_GBps": float(moved / max((kms[0] + kms[1]) / 1e3, 1e-12) / 1e9)}
+    # the whole step against HBM at the two per-vertex byte counts of the
+    # method: the direction-wise sweep schedule (2D 44 B, 3D 72 B: one read of
+    # each block's state and weights per sweep plus the intermediates the
+    # sweeps hand on) and the lower bound (every state array read and written
+    # once, w and the weights read once: 2D 28 B, 3D 40 B)
+    if args.algo == "aar" and not conn:
+        vps = value / world * 1e6                  # this GPU's vertex-iterations per second
+        sched_b, lb_b = (72, 40) if ndim == 3 else (44, 28)
+        roofline["step_frac_at_schedule_bytes"] = {"bytes_per_vertex_iter": sched_b,
+                                                   "frac": vps * sched_b / (peak * 1e9)}
+        roofline["step_frac_at_lower_bound_bytes"] = {"bytes_per_vertex_iter": lb_b,
+                                                      "frac": vps * lb_b / (peak * 1e9)}
 
     # end to end through the C-ABI with host buffers: H2D inputs, solve, D2H labels
     e2e_solver = tvcut.Solver(dims, algo=algo, dtype=tvcut.F32, check_every=iters, stream=stream.cuda_stream,
