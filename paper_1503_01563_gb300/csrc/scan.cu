@@ -26,6 +26,8 @@
 // BCD and FISTA (Sec. 4.1) hold the duals y_k; their passes form the point to
 // project (bcd_prepare_kernel, fista_prepare_kernel, prep8_kernel) and the
 // scan writes the projection v - prox(v) directly (SHADOW).
+#include <mutex>
+
 #include "tvcut_internal.cuh"
 #include "taut_string.cuh"
 #include "funnel.cuh"
@@ -120,7 +122,11 @@ cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s)
 // L+1 (or any later lane) recorded; that lane's results after the bend are
 // then exact, and lane L rewrites every position before it.  Lane 0 is
 // exact, so following merges from lane 0 reaches the chain end through
-// verified lanes only; lanes not on that path are overwritten.
+// verified lanes only; lanes not on that path are overwritten.  A launch
+// lasts as long as its slowest chain's critical path (piece, continuation,
+// rewrite); where shared memory allows it without another wave of CTAs,
+// each lane keeps its continuation's segments so that the rewrite only
+// stores them (the same values: the same scan from the same state).
 
 // Advance one lane's scan through positions st.i .. stop-1 (data in shared
 // memory, skewed).  on_bend(s, e, d, t) is called for every finished segment
@@ -190,19 +196,32 @@ __device__ __forceinline__ int lane_scan(LaneState<T>& st, int m, int stop, cons
 }
 
 
+// A continuation's finished segments (end, value), kept by phase 2 so that
+// phase 3 writes them instead of scanning the continuation again; a lane
+// whose continuation has more than kContSegs segments scans it again.
+constexpr int kContSegs = 16;
+
+template <typename T>
+struct ContSeg {
+    int e;
+    T t;
+};
+
 // G lanes share a chain (G = 4 .. 32, a warp holds 32/G chains); a CTA holds
 // nc chains, nc * G threads.  With few chains G = 32 spreads each chain over a
 // whole warp; with many, a smaller G does less speculative work per chain.
-template <typename T, bool SHADOW, int G>
+template <typename T, bool SHADOW, int G, bool LIST>
 __global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
 {
     extern __shared__ __align__(16) unsigned char wsm[];
+    constexpr int KS = LIST ? kContSegs : 0;
     int k = 0;
     while (k + 1 < A.naxes && blockIdx.x >= A.ax[k + 1].block_begin) ++k;
     const ScanAxis<T>& X = A.ax[k];
     const int m = X.m;
     const int pitch = skew32(m) + 1;
-    T* sv = (T*)wsm;
+    ContSeg<T>* sg = (ContSeg<T>*)wsm;                        // KS per lane
+    T* sv = (T*)(sg + (size_t)nc * G * KS);
     T* sa = sv + (size_t)nc * pitch;
     uint8_t* code = (uint8_t*)(sa + (size_t)nc * pitch);
     const int64_t c0 = (int64_t)(blockIdx.x - X.block_begin) * nc;
@@ -261,11 +280,17 @@ __global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
         });
     }
     __syncwarp();
-    // phase 2: continue until a bend recorded by a later piece (or the end)
-    int merge = m - 1;
+    // phase 2: continue until a bend recorded by a later piece (or the end),
+    // keeping the segments passed
+    int merge = m - 1, nseg = 0;
+    ContSeg<T>* seg = sg + (size_t)threadIdx.x * KS;
     if (active && !lastp) {
         LaneState<T> s2 = st;
-        lane_scan<T>(s2, m, m, cv, ca, [&](int, int e, int d, T) {
+        lane_scan<T>(s2, m, m, cv, ca, [&](int, int e, int d, T t) {
+            if constexpr (LIST) {
+                if (nseg < KS) seg[nseg] = ContSeg<T>{e, t};
+            }
+            ++nseg;
             if (d && e >= p1 && cc[e] == (uint8_t)d) {
                 merge = e;
                 return true;
@@ -286,12 +311,22 @@ __global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
         const int nv = __shfl_sync(0xffffffffu, target, glane0 + (live ? v : 0));
         if (live) v = nv;
     }
-    // phase 3: verified lanes rewrite their continuation up to the merge bend
+    // phase 3: verified lanes write their continuation up to the merge bend
+    // (the same segments phase 2 passed, from the same state)
     if (((verified >> gl) & 1u) && active && !lastp) {
-        lane_scan<T>(st, m, m, cv, ca, [&](int s0, int e, int, T t) {
-            write_seg(s0, e, t);
-            return e >= merge;
-        });
+        if (LIST && nseg <= KS) {
+            int s0 = st.s;
+            for (int q = 0; q < nseg; ++q) {
+                const ContSeg<T> sq = seg[q];
+                write_seg(s0, sq.e, sq.t);
+                s0 = sq.e + 1;
+            }
+        } else {
+            lane_scan<T>(st, m, m, cv, ca, [&](int s0, int e, int, T t) {
+                write_seg(s0, e, t);
+                return e >= merge;
+            });
+        }
     }
 }
 
@@ -525,40 +560,109 @@ static cudaError_t launch_fscan(const ScanArgs<T>& wrp, int G, int mmax, cudaStr
 }
 
 template <typename T>
-static size_t wscan_smem(int m, int nc)
+static size_t wscan_smem(int m, int nc, int G, bool list)
 {
-    return (size_t)nc * (2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
+    return (size_t)nc * ((size_t)G * (list ? kContSegs : 0) * sizeof(ContSeg<T>) +
+                         2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
 }
 
 // Chains per CTA for G lanes per chain: at most 256 threads, whole warps, and
 // shared memory within 100 KB (two CTAs per SM); 0 if a warp's chains do not fit.
 template <typename T>
-static int wscan_chains(int m, int G)
+static int wscan_chains(int m, int G, bool list)
 {
     const int per_warp = 32 / G;
     int nc = 256 / G;
-    while (nc > per_warp && wscan_smem<T>(m, nc) > 100 * 1024) nc -= per_warp;
-    return wscan_smem<T>(m, nc) <= 200 * 1024 ? nc : 0;
+    while (nc > per_warp && wscan_smem<T>(m, nc, G, list) > 100 * 1024) nc -= per_warp;
+    return wscan_smem<T>(m, nc, G, list) <= 200 * 1024 ? nc : 0;
 }
 
-template <typename T, bool SHADOW>
-static cudaError_t launch_wscan(const ScanArgs<T>& wrp, int G, int nc, int64_t blocks, size_t smem, cudaStream_t s)
+template <typename T, bool SHADOW, bool LIST>
+static void (*wscan_fn(int G))(ScanArgs<T>, int)
 {
-    static bool attr_set[64][4] = {};
+    return G == 32 ? wscan_kernel<T, SHADOW, 32, LIST>
+         : G == 16 ? wscan_kernel<T, SHADOW, 16, LIST>
+         : G == 8 ? wscan_kernel<T, SHADOW, 8, LIST>
+                  : wscan_kernel<T, SHADOW, 4, LIST>;
+}
+
+// Launch plan of the lane-group scan for G lanes per chain: with or without
+// the continuation lists (they spare phase 3 a second scan of every verified
+// continuation but take shared memory), whichever needs fewer waves of CTAs
+// over the GPU (the lists on a tie).  Occupancy comes from the runtime (the
+// kernels' registers and shared memory); plans are cached per shape.
+struct WscanPlan {
+    bool list;
+    int nc;
+    int64_t blocks;
+    size_t smem;
+};
+
+template <typename T, bool SHADOW>
+static cudaError_t wscan_plan(const ScanArgs<T>& wrp, int G, int mmax, WscanPlan& P)
+{
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    int64_t nchains = 0;
+    for (int k = 0; k < wrp.naxes; ++k) nchains += wrp.ax[k].nchains;
+    struct Key {
+        int dev, G, mmax, naxes;
+        int64_t nchains;
+    };
+    static Key keys[8];
+    static WscanPlan plans[8];
+    static int nkeys = 0, next = 0;
+    static std::mutex mu;                  // handles on other host threads share the cache
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < nkeys; ++i)
+        if (keys[i].dev == dev && keys[i].G == G && keys[i].mmax == mmax && keys[i].naxes == wrp.naxes &&
+            keys[i].nchains == nchains) {
+            P = plans[i];
+            return cudaSuccess;
+        }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    static bool attr_set[64][4][2] = {};
     const int gi = G == 32 ? 0 : G == 16 ? 1 : G == 8 ? 2 : 3;
-    void (*fn)(ScanArgs<T>, int) = G == 32 ? wscan_kernel<T, SHADOW, 32>
-                                   : G == 16 ? wscan_kernel<T, SHADOW, 16>
-                                   : G == 8 ? wscan_kernel<T, SHADOW, 8>
-                                            : wscan_kernel<T, SHADOW, 4>;
-    if (dev < 0 || dev >= 64 || !attr_set[dev][gi]) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int64_t waves[2] = {-1, -1};
+    WscanPlan cand[2];
+    for (int li = 0; li < 2; ++li) {
+        const bool list = li == 1;
+        const int nc = wscan_chains<T>(mmax, G, list);
+        if (nc == 0) continue;
+        int64_t blocks = 0;
+        for (int k = 0; k < wrp.naxes; ++k) blocks += (wrp.ax[k].nchains + nc - 1) / nc;
+        const size_t smem = wscan_smem<T>(mmax, nc, G, list);
+        void (*fn)(ScanArgs<T>, int) = list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
+        if (dev < 0 || dev >= 64 || !attr_set[dev][gi][li]) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) attr_set[dev][gi][li] = true;
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nc * G, smem);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev][gi] = true;
+        if (per_sm < 1) continue;
+        waves[li] = (blocks + (int64_t)per_sm * sms - 1) / ((int64_t)per_sm * sms);
+        cand[li] = WscanPlan{list, nc, blocks, smem};
     }
-    fn<<<(unsigned)blocks, nc * G, smem, s>>>(wrp, nc);
+    if (waves[1] >= 0 && (waves[0] < 0 || waves[1] <= waves[0])) P = cand[1];
+    else if (waves[0] >= 0) P = cand[0];
+    else return cudaErrorInvalidConfiguration;
+    keys[next] = Key{dev, G, mmax, wrp.naxes, nchains};
+    plans[next] = P;
+    next = (next + 1) % 8;
+    if (nkeys < 8) ++nkeys;
+    return cudaSuccess;
+}
+
+template <typename T, bool SHADOW>
+static cudaError_t launch_wscan(const ScanArgs<T>& wrp, int G, const WscanPlan& P, cudaStream_t s)
+{
+    void (*fn)(ScanArgs<T>, int) = P.list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
+    fn<<<(unsigned)P.blocks, P.nc * G, P.smem, s>>>(wrp, P.nc);
     return cudaGetLastError();
 }
 
@@ -608,9 +712,9 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
     thr.shadow = wrp.shadow = A.shadow;
     for (int k = 0; k < A.naxes; ++k) {
         const ScanAxis<T>& X = A.ax[k];
-        bool warp = X.m >= 64 && total <= 98304 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        bool warp = X.m >= 64 && total <= 98304 && wscan_smem<T>(X.m, 1, 32, false) <= 200 * 1024;
         if (A.force == 1) warp = false;
-        if (A.force >= 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1) <= 200 * 1024;
+        if (A.force >= 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1, 32, false) <= 200 * 1024;
         if (warp) wrp.ax[wrp.naxes++] = X;
         else thr.ax[thr.naxes++] = X;
     }
@@ -643,20 +747,17 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
         int G = 32;
         if (A.force == 0) while (G > 4 && mmax < 16 * G) G >>= 1;
         else G = A.force == 3 ? 16 : A.force == 4 ? 8 : A.force == 5 ? 4 : 32;
-        int nc = wscan_chains<T>(mmax, G);
-        if (nc == 0) {                             // long chains: whole warps
-            G = 32;
-            nc = wscan_chains<T>(mmax, G);
-        }
+        if (wscan_chains<T>(mmax, G, false) == 0) G = 32;   // long chains: whole warps
+        WscanPlan P;
+        cudaError_t e = A.shadow ? wscan_plan<T, true>(wrp, G, mmax, P) : wscan_plan<T, false>(wrp, G, mmax, P);
+        if (e != cudaSuccess) return e;
         int64_t blocks = 0;
         for (int k = 0; k < wrp.naxes; ++k) {
             wrp.ax[k].block_begin = blocks;
-            blocks += (wrp.ax[k].nchains + nc - 1) / nc;
+            blocks += (wrp.ax[k].nchains + P.nc - 1) / P.nc;
         }
-        const size_t smem = wscan_smem<T>(mmax, nc);
         if (blocks > 0)
-            return A.shadow ? launch_wscan<T, true>(wrp, G, nc, blocks, smem, s)
-                            : launch_wscan<T, false>(wrp, G, nc, blocks, smem, s);
+            return A.shadow ? launch_wscan<T, true>(wrp, G, P, s) : launch_wscan<T, false>(wrp, G, P, s);
     }
     return cudaSuccess;
 }
