@@ -7,7 +7,7 @@
 //           (Sec. 4.2: Pi_K splits into the Pi_{K_k}), so all axes share one
 //           launch; a thread (reading weights padded to the state layout, so
 //           that each element is loaded one step ahead), or a group of 4-32
-//           lanes, owns one chain.  The prox is the taut string of Sec. 3.2
+//           lanes (lanescan.cu), owns one chain.  The prox is the taut string of Sec. 3.2
 //           in local form (see scan_chain).  Each block's state is stored so
 //           that consecutive chains are consecutive in memory ("chain-major"):
 //           the natural row-major layout already is for every axis but the
@@ -26,29 +26,12 @@
 // BCD and FISTA (Sec. 4.1) hold the duals y_k; their passes form the point to
 // project (bcd_prepare_kernel, fista_prepare_kernel, prep8_kernel) and the
 // scan writes the projection v - prox(v) directly (SHADOW).
-#include <mutex>
-
 #include "tvcut_internal.cuh"
 #include "taut_string.cuh"
-#include "funnel.cuh"
 
 namespace tvcut {
 
 constexpr int kScanThreads = 128;
-
-__device__ __forceinline__ void scan_cp_async(void* smem, const void* gmem, int bytes)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-template <typename T>
-__device__ __forceinline__ void scan_cp_elem(T* smem, const T* gmem) { scan_cp_async(smem, gmem, (int)sizeof(T)); }
-__device__ __forceinline__ void scan_cp_wait()
-{
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 // PADDED: every axis carries its weights in the state's layout (ap), so the
 // scan loads each element one step ahead (scan_chain_padded).  Used for the
@@ -109,563 +92,6 @@ cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// ---- lane-group (speculative pieces) scan -------------------------------------
-//
-// For few, long chains (a 2D grid has only H + W of them) one thread per chain
-// leaves the GPU idle, so G lanes (4 .. 32, the kernel's template parameter)
-// share one chain: lane L scans piece L of G from a guessed state (a segment starts at the piece start with multiplier
-// 0; exact for lane 0) and records every bend it finds (position e and
-// direction).  After a bend at e the scan state is fixed (the next segment
-// starts at e+1 with multiplier +-a_e), so a lane's trajectory is the true one
-// from the first bend it shares with the true scan.  Lane L then continues
-// from its own piece end into piece L+1 until it produces a bend that lane
-// L+1 (or any later lane) recorded; that lane's results after the bend are
-// then exact, and lane L rewrites every position before it.  Lane 0 is
-// exact, so following merges from lane 0 reaches the chain end through
-// verified lanes only; lanes not on that path are overwritten.  A launch
-// lasts as long as its slowest chain's critical path (piece, continuation,
-// rewrite); where shared memory allows it without another wave of CTAs,
-// each lane keeps its continuation's segments so that the rewrite only
-// stores them (the same values: the same scan from the same state).
-
-// Advance one lane's scan through positions st.i .. stop-1 (data in shared
-// memory, skewed).  on_bend(s, e, d, t) is called for every finished segment
-// [s, e] with value t (d = 1: the string bends up at e, 2: down, 0: chain end)
-// and returns true to stop.  Returns 0 at stop, 1 when stopped by on_bend,
-// 2 at the chain end.
-template <typename T, class OnBend>
-__device__ __forceinline__ int lane_scan(LaneState<T>& st, int m, int stop, const T* sv, const T* sa, OnBend on_bend)
-{
-    for (;;) {
-        if (st.i >= stop) return 0;
-        const int i = st.i;
-        const T vi = sv[skew32(i)];
-        const T Ai = (i < m - 1) ? sa[skew32(i)] : T(0);
-        bool init = (i == st.s);
-        if (!init) {
-            st.uh += st.th - vi;
-            st.ul += st.tl - vi;
-            const bool bhi = st.uh < -Ai;
-            const bool blo = !bhi && st.ul > Ai;
-            if (bhi || blo) {
-                const int e = bhi ? st.ih : st.il;
-                const T t = bhi ? st.th : st.tl;
-                st.u0 = bhi ? st.ah : -st.al;
-                const int s_old = st.s;
-                st.s = e + 1;
-                if (on_bend(s_old, e, bhi ? 1 : 2, t)) {
-                    st.i = st.s;
-                    return 1;
-                }
-                if (st.s < i) {
-                    st.i = st.s;
-                    continue;
-                }
-                init = true;
-            } else {
-                const int len = i - st.s + 1;
-                if (st.uh > Ai) {
-                    st.th -= div_len<T>(st.uh - Ai, len);
-                    st.uh = Ai;
-                    st.ih = i;
-                    st.ah = Ai;
-                }
-                if (st.ul < -Ai) {
-                    st.tl += div_len<T>(-Ai - st.ul, len);
-                    st.ul = -Ai;
-                    st.il = i;
-                    st.al = Ai;
-                }
-            }
-        }
-        if (init) {
-            st.th = vi + Ai - st.u0;
-            st.tl = vi - Ai - st.u0;
-            st.uh = Ai;
-            st.ul = -Ai;
-            st.ih = st.il = i;
-            st.ah = st.al = Ai;
-        }
-        if (i == m - 1) {
-            on_bend(st.s, m - 1, 0, st.th);
-            st.i = m;
-            return 2;
-        }
-        st.i = i + 1;
-    }
-}
-
-
-// A continuation's finished segments (end, value), kept by phase 2 so that
-// phase 3 writes them instead of scanning the continuation again; a lane
-// whose continuation has more than kContSegs segments scans it again.
-constexpr int kContSegs = 16;
-
-template <typename T>
-struct ContSeg {
-    int e;
-    T t;
-};
-
-// G lanes share a chain (G = 4 .. 32, a warp holds 32/G chains); a CTA holds
-// nc chains, nc * G threads.  With few chains G = 32 spreads each chain over a
-// whole warp; with many, a smaller G does less speculative work per chain.
-template <typename T, bool SHADOW, int G, bool LIST>
-__global__ void __launch_bounds__(256) wscan_kernel(ScanArgs<T> A, int nc)
-{
-    extern __shared__ __align__(16) unsigned char wsm[];
-    constexpr int KS = LIST ? kContSegs : 0;
-    int k = 0;
-    while (k + 1 < A.naxes && blockIdx.x >= A.ax[k + 1].block_begin) ++k;
-    const ScanAxis<T>& X = A.ax[k];
-    const int m = X.m;
-    const int pitch = skew32(m) + 1;
-    ContSeg<T>* sg = (ContSeg<T>*)wsm;                        // KS per lane
-    T* sv = (T*)(sg + (size_t)nc * G * KS);
-    T* sa = sv + (size_t)nc * pitch;
-    uint8_t* code = (uint8_t*)(sa + (size_t)nc * pitch);
-    const int64_t c0 = (int64_t)(blockIdx.x - X.block_begin) * nc;
-    const int nvalid = (int)min((int64_t)nc, X.nchains - c0);
-
-    auto gbase = [&](int64_t c, int64_t& vb, int64_t& ab, int64_t& st) {
-        if (X.transposed) { vb = c; ab = c; st = X.nchains; }
-        else {
-            const int64_t o = c / X.inner, q = c - o * X.inner;
-            vb = o * (int64_t)m * X.inner + q;
-            ab = o * (int64_t)(m - 1) * X.inner + q;
-            st = X.inner;
-        }
-    };
-    // stage the CTA's chains (chain index fastest: consecutive chains are
-    // consecutive in global memory) and clear the bend codes
-    for (int idx = threadIdx.x; idx < nc * m; idx += blockDim.x) {
-        const int c = idx % nc, j = idx / nc;
-        code[c * m + j] = 0;
-        if (c >= nvalid) continue;
-        int64_t vb, ab, st;
-        gbase(c0 + c, vb, ab, st);
-        scan_cp_elem(sv + c * pitch + skew32(j), X.v + vb + (int64_t)j * st);
-        if (j < m - 1) scan_cp_elem(sa + c * pitch + skew32(j), X.a + ab + (int64_t)j * st);
-    }
-    scan_cp_wait();
-    __syncthreads();
-
-    // lanes of chains past the end stay (inactive) for the group shuffles
-    const int ch = threadIdx.x / G, gl = threadIdx.x % G;
-    const int glane0 = (threadIdx.x & 31) & ~(G - 1);     // first warp lane of the group
-    const bool valid = ch < nvalid;
-    int64_t vb = 0, ab = 0, gst = 0;
-    if (valid) gbase(c0 + ch, vb, ab, gst);
-    T* gx = X.x + vb;
-    const T* cv = sv + ch * pitch;
-    const T* ca = sa + ch * pitch;
-    uint8_t* cc = code + ch * m;
-    const int lp = (m + G - 1) / G;               // piece length
-    const int npieces = valid ? (m + lp - 1) / lp : 0;
-    const int p0 = gl * lp;
-    const int p1 = min(m, p0 + lp);
-    const bool active = gl < npieces;
-    const bool lastp = gl == npieces - 1;
-    auto write_seg = [&](int from, int to, T t) {
-        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = SHADOW ? cv[skew32(j)] - t : t;
-    };
-
-    // phase 1: every piece from a guessed state
-    LaneState<T> st{p0, p0, p0, p0, T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    if (active) {
-        lane_scan<T>(st, m, lastp ? m : p1, cv, ca, [&](int s0, int e, int d, T t) {
-            if (d) cc[e] = (uint8_t)d;
-            write_seg(s0, e, t);
-            return false;
-        });
-    }
-    __syncwarp();
-    // phase 2: continue until a bend recorded by a later piece (or the end),
-    // keeping the segments passed
-    int merge = m - 1, nseg = 0;
-    ContSeg<T>* seg = sg + (size_t)threadIdx.x * KS;
-    if (active && !lastp) {
-        LaneState<T> s2 = st;
-        lane_scan<T>(s2, m, m, cv, ca, [&](int, int e, int d, T t) {
-            if constexpr (LIST) {
-                if (nseg < KS) seg[nseg] = ContSeg<T>{e, t};
-            }
-            ++nseg;
-            if (d && e >= p1 && cc[e] == (uint8_t)d) {
-                merge = e;
-                return true;
-            }
-            return false;
-        });
-    }
-    // verified pieces: lane 0, then the piece holding each verified lane's
-    // merge bend (pieces skipped over are rewritten by that continuation);
-    // G steps for every group, so that the whole warp shuffles together
-    const int target = (active && !lastp && merge < m - 1) ? merge / lp : npieces;
-    unsigned verified = 0;
-    int v = 0;
-#pragma unroll 1
-    for (int it = 0; it < G; ++it) {
-        const bool live = v < npieces;
-        if (live) verified |= 1u << v;
-        const int nv = __shfl_sync(0xffffffffu, target, glane0 + (live ? v : 0));
-        if (live) v = nv;
-    }
-    // phase 3: verified lanes write their continuation up to the merge bend
-    // (the same segments phase 2 passed, from the same state)
-    if (((verified >> gl) & 1u) && active && !lastp) {
-        if (LIST && nseg <= KS) {
-            int s0 = st.s;
-            for (int q = 0; q < nseg; ++q) {
-                const ContSeg<T> sq = seg[q];
-                write_seg(s0, sq.e, sq.t);
-                s0 = sq.e + 1;
-            }
-        } else {
-            lane_scan<T>(st, m, m, cv, ca, [&](int s0, int e, int, T t) {
-                write_seg(s0, e, t);
-                return e >= merge;
-            });
-        }
-    }
-}
-
-// ---- lane-group scan with the funnel (no rescans) --------------------------
-//
-// The phases of wscan_kernel with the funnel form of the taut string
-// (funnel.cuh) in place of the local form: a lane's cost is then linear in
-// the elements it passes, where the local form restarts behind every bend
-// and is quadratic on the long plateaus of segmentation iterates.  Phase 2
-// keeps the segments of its continuation (up to kFunnelSegs), so that phase 3
-// writes them instead of scanning again.  A lane whose hull chain fills
-// (kFunnelQ vertices), or whose continuation has more segments, falls back to
-// the local form from its apex.
-
-constexpr int kFunnelQ = 16;
-constexpr int kFunnelSegs = 16;
-
-template <typename T>
-struct FSeg {
-    int e;
-    T t;
-};
-
-template <typename T, int G>
-__host__ __device__ __forceinline__ size_t fscan_lane_bytes()
-{
-    return (size_t)G * (2 * kFunnelQ * sizeof(FVert<T>) + kFunnelSegs * sizeof(FSeg<T>));
-}
-
-template <typename T, bool SHADOW, int G>
-__global__ void __launch_bounds__(256) fscan_kernel(ScanArgs<T> A, int nc)
-{
-    extern __shared__ __align__(16) unsigned char fsm[];
-    int k = 0;
-    while (k + 1 < A.naxes && blockIdx.x >= A.ax[k + 1].block_begin) ++k;
-    const ScanAxis<T>& X = A.ax[k];
-    const int m = X.m;
-    const int pitch = skew32(m) + 1;
-    FVert<T>* dq = (FVert<T>*)fsm;                                    // 2 rings per lane
-    FSeg<T>* sg = (FSeg<T>*)(dq + (size_t)nc * G * 2 * kFunnelQ);   // continuation segments per lane
-    T* sv = (T*)(sg + (size_t)nc * G * kFunnelSegs);
-    T* sa = sv + (size_t)nc * pitch;
-    uint8_t* code = (uint8_t*)(sa + (size_t)nc * pitch);
-    const int64_t c0 = (int64_t)(blockIdx.x - X.block_begin) * nc;
-    const int nvalid = (int)min((int64_t)nc, X.nchains - c0);
-
-    auto gbase = [&](int64_t c, int64_t& vb, int64_t& ab, int64_t& st) {
-        if (X.transposed) { vb = c; ab = c; st = X.nchains; }
-        else {
-            const int64_t o = c / X.inner, q = c - o * X.inner;
-            vb = o * (int64_t)m * X.inner + q;
-            ab = o * (int64_t)(m - 1) * X.inner + q;
-            st = X.inner;
-        }
-    };
-    for (int idx = threadIdx.x; idx < nc * m; idx += blockDim.x) {
-        const int c = idx % nc, j = idx / nc;
-        code[c * m + j] = 0;
-        if (c >= nvalid) continue;
-        int64_t vb, ab, st;
-        gbase(c0 + c, vb, ab, st);
-        scan_cp_elem(sv + c * pitch + skew32(j), X.v + vb + (int64_t)j * st);
-        if (j < m - 1) scan_cp_elem(sa + c * pitch + skew32(j), X.a + ab + (int64_t)j * st);
-    }
-    scan_cp_wait();
-    __syncthreads();
-
-    const int ch = threadIdx.x / G, gl = threadIdx.x % G;
-    const int glane0 = (threadIdx.x & 31) & ~(G - 1);
-    const bool valid = ch < nvalid;
-    int64_t vb = 0, ab = 0, gst = 0;
-    if (valid) gbase(c0 + ch, vb, ab, gst);
-    T* gx = X.x + vb;
-    const T* cv = sv + ch * pitch;
-    const T* ca = sa + ch * pitch;
-    uint8_t* cc = code + ch * m;
-    FVert<T>* U = dq + (size_t)threadIdx.x * 2 * kFunnelQ;
-    FVert<T>* L = U + kFunnelQ;
-    FSeg<T>* seg = sg + (size_t)threadIdx.x * kFunnelSegs;
-    const int lp = (m + G - 1) / G;
-    const int npieces = valid ? (m + lp - 1) / lp : 0;
-    const int p0 = gl * lp;
-    const int p1 = min(m, p0 + lp);
-    const bool active = gl < npieces;
-    const bool lastp = gl == npieces - 1;
-    auto write_seg = [&](int from, int to, T t) {
-        for (int j = from; j <= to; ++j) gx[(int64_t)j * gst] = SHADOW ? cv[skew32(j)] - t : t;
-    };
-
-    // phase 1: every piece from a guessed state (a segment starting at the
-    // piece start with multiplier 0; exact for piece 0)
-    FunnelState<T> f = funnel_start<T>(p0);
-    LaneState<T> st{};
-    bool loc = false;                 // the lane runs the local form from here on
-    LaneState<T> open{};              // restart state of the open segment at the piece end
-    if (active) {
-        auto rec = [&](int s0, int e, int d, T t) {
-            if (d) cc[e] = (uint8_t)d;
-            write_seg(s0, e, t);
-            return false;
-        };
-        const int stop = lastp ? m : p1;
-        if (funnel_scan<T, kFunnelQ>(f, m, stop, cv, ca, U, L, rec) == 3) {
-            st = funnel_to_local<T>(f, ca);
-            loc = true;
-            lane_scan<T>(st, m, stop, cv, ca, rec);
-        }
-        if (loc) open = LaneState<T>{st.s, st.s, st.s, st.s, st.u0, T(0), T(0), T(0), T(0), T(0), T(0)};
-        else open = funnel_to_local<T>(f, ca);
-    }
-    __syncwarp();
-    // phase 2: continue until a bend recorded by a later piece (or the end),
-    // keeping the segments passed
-    int merge = m - 1, nseg = 0;
-    if (active && !lastp) {
-        auto keep = [&](int, int e, int d, T t) {
-            if (nseg < kFunnelSegs) seg[nseg] = FSeg<T>{e, t};
-            ++nseg;
-            if (d && e >= p1 && cc[e] == (uint8_t)d) {
-                merge = e;
-                return true;
-            }
-            return false;
-        };
-        if (!loc && funnel_scan<T, kFunnelQ>(f, m, m, cv, ca, U, L, keep) == 3) {
-            st = funnel_to_local<T>(f, ca);
-            loc = true;
-        }
-        if (loc) lane_scan<T>(st, m, m, cv, ca, keep);
-    }
-    const int target = (active && !lastp && merge < m - 1) ? merge / lp : npieces;
-    unsigned verified = 0;
-    int v = 0;
-#pragma unroll 1
-    for (int it = 0; it < G; ++it) {
-        const bool live = v < npieces;
-        if (live) verified |= 1u << v;
-        const int nv = __shfl_sync(0xffffffffu, target, glane0 + (live ? v : 0));
-        if (live) v = nv;
-    }
-    // phase 3: verified lanes write their continuation up to the merge bend
-    if (((verified >> gl) & 1u) && active && !lastp) {
-        if (nseg <= kFunnelSegs) {
-            int s0 = open.s;
-            for (int q = 0; q < nseg; ++q) {
-                const FSeg<T> sq = seg[q];
-                write_seg(s0, sq.e, sq.t);
-                s0 = sq.e + 1;
-            }
-        } else {
-            lane_scan<T>(open, m, m, cv, ca, [&](int s0, int e, int, T t) {
-                write_seg(s0, e, t);
-                return e >= merge;
-            });
-        }
-    }
-}
-
-template <typename T, int G>
-static size_t fscan_smem(int m, int nc)
-{
-    return (size_t)nc * (fscan_lane_bytes<T, G>() + 2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
-}
-
-// Chains per CTA for the funnel scan: whole warps, at most 256 threads, and
-// as many chains per SM as the shared memory allows (227 KB per SM).
-template <typename T, int G>
-static int fscan_chains(int m)
-{
-    const int per_warp = 32 / G;
-    int best = 0, best_per_sm = 0;
-    for (int nc = per_warp; nc * G <= 256; nc += per_warp) {
-        const size_t b = fscan_smem<T, G>(m, nc);
-        if (b > 227 * 1024) break;
-        const int per_sm = (int)((227 * 1024) / b) * nc;
-        if (per_sm > best_per_sm) { best = nc; best_per_sm = per_sm; }
-    }
-    return best;
-}
-
-template <typename T, bool SHADOW, int G>
-static cudaError_t launch_fscan_g(const ScanArgs<T>& wrp, int mmax, cudaStream_t s)
-{
-    const int nc = fscan_chains<T, G>(mmax);
-    if (nc == 0) return cudaErrorInvalidValue;
-    ScanArgs<T> a = wrp;
-    int64_t blocks = 0;
-    for (int k = 0; k < a.naxes; ++k) {
-        a.ax[k].block_begin = blocks;
-        blocks += (a.ax[k].nchains + nc - 1) / nc;
-    }
-    if (blocks == 0) return cudaSuccess;
-    const size_t smem = fscan_smem<T, G>(mmax, nc);
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(fscan_kernel<T, SHADOW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
-    fscan_kernel<T, SHADOW, G><<<(unsigned)blocks, nc * G, smem, s>>>(a, nc);
-    return cudaGetLastError();
-}
-
-// Lanes per chain for the funnel scan: pieces of at least 16 elements, 4 to
-// 32 lanes, and fewer lanes when a chain's staging does not fit.
-template <typename T>
-static int fscan_lanes(int mmax)
-{
-    int G = 32;
-    while (G > 4 && mmax < 16 * G) G >>= 1;
-    auto fits = [&](int g) {
-        return g == 32 ? fscan_chains<T, 32>(mmax) > 0 : g == 16 ? fscan_chains<T, 16>(mmax) > 0
-             : g == 8 ? fscan_chains<T, 8>(mmax) > 0 : fscan_chains<T, 4>(mmax) > 0;
-    };
-    while (G > 4 && !fits(G)) G >>= 1;
-    return fits(G) ? G : 0;
-}
-
-template <typename T, bool SHADOW>
-static cudaError_t launch_fscan(const ScanArgs<T>& wrp, int G, int mmax, cudaStream_t s)
-{
-    switch (G) {
-    case 32: return launch_fscan_g<T, SHADOW, 32>(wrp, mmax, s);
-    case 16: return launch_fscan_g<T, SHADOW, 16>(wrp, mmax, s);
-    case 8: return launch_fscan_g<T, SHADOW, 8>(wrp, mmax, s);
-    default: return launch_fscan_g<T, SHADOW, 4>(wrp, mmax, s);
-    }
-}
-
-template <typename T>
-static size_t wscan_smem(int m, int nc, int G, bool list)
-{
-    return (size_t)nc * ((size_t)G * (list ? kContSegs : 0) * sizeof(ContSeg<T>) +
-                         2 * (size_t)(skew32(m) + 1) * sizeof(T) + (size_t)m);
-}
-
-// Chains per CTA for G lanes per chain: at most 256 threads, whole warps, and
-// shared memory within 100 KB (two CTAs per SM); 0 if a warp's chains do not fit.
-template <typename T>
-static int wscan_chains(int m, int G, bool list)
-{
-    const int per_warp = 32 / G;
-    int nc = 256 / G;
-    while (nc > per_warp && wscan_smem<T>(m, nc, G, list) > 100 * 1024) nc -= per_warp;
-    return wscan_smem<T>(m, nc, G, list) <= 200 * 1024 ? nc : 0;
-}
-
-template <typename T, bool SHADOW, bool LIST>
-static void (*wscan_fn(int G))(ScanArgs<T>, int)
-{
-    return G == 32 ? wscan_kernel<T, SHADOW, 32, LIST>
-         : G == 16 ? wscan_kernel<T, SHADOW, 16, LIST>
-         : G == 8 ? wscan_kernel<T, SHADOW, 8, LIST>
-                  : wscan_kernel<T, SHADOW, 4, LIST>;
-}
-
-// Launch plan of the lane-group scan for G lanes per chain: with or without
-// the continuation lists (they spare phase 3 a second scan of every verified
-// continuation but take shared memory), whichever needs fewer waves of CTAs
-// over the GPU (the lists on a tie).  Occupancy comes from the runtime (the
-// kernels' registers and shared memory); plans are cached per shape.
-struct WscanPlan {
-    bool list;
-    int nc;
-    int64_t blocks;
-    size_t smem;
-};
-
-template <typename T, bool SHADOW>
-static cudaError_t wscan_plan(const ScanArgs<T>& wrp, int G, int mmax, WscanPlan& P)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int64_t nchains = 0;
-    for (int k = 0; k < wrp.naxes; ++k) nchains += wrp.ax[k].nchains;
-    struct Key {
-        int dev, G, mmax, naxes;
-        int64_t nchains;
-    };
-    static Key keys[8];
-    static WscanPlan plans[8];
-    static int nkeys = 0, next = 0;
-    static std::mutex mu;                  // handles on other host threads share the cache
-    std::lock_guard<std::mutex> lock(mu);
-    for (int i = 0; i < nkeys; ++i)
-        if (keys[i].dev == dev && keys[i].G == G && keys[i].mmax == mmax && keys[i].naxes == wrp.naxes &&
-            keys[i].nchains == nchains) {
-            P = plans[i];
-            return cudaSuccess;
-        }
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    static bool attr_set[64][4][2] = {};
-    const int gi = G == 32 ? 0 : G == 16 ? 1 : G == 8 ? 2 : 3;
-    int64_t waves[2] = {-1, -1};
-    WscanPlan cand[2];
-    for (int li = 0; li < 2; ++li) {
-        const bool list = li == 1;
-        const int nc = wscan_chains<T>(mmax, G, list);
-        if (nc == 0) continue;
-        int64_t blocks = 0;
-        for (int k = 0; k < wrp.naxes; ++k) blocks += (wrp.ax[k].nchains + nc - 1) / nc;
-        const size_t smem = wscan_smem<T>(mmax, nc, G, list);
-        void (*fn)(ScanArgs<T>, int) = list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
-        if (dev < 0 || dev >= 64 || !attr_set[dev][gi][li]) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) attr_set[dev][gi][li] = true;
-        }
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nc * G, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) continue;
-        waves[li] = (blocks + (int64_t)per_sm * sms - 1) / ((int64_t)per_sm * sms);
-        cand[li] = WscanPlan{list, nc, blocks, smem};
-    }
-    if (waves[1] >= 0 && (waves[0] < 0 || waves[1] <= waves[0])) P = cand[1];
-    else if (waves[0] >= 0) P = cand[0];
-    else return cudaErrorInvalidConfiguration;
-    keys[next] = Key{dev, G, mmax, wrp.naxes, nchains};
-    plans[next] = P;
-    next = (next + 1) % 8;
-    if (nkeys < 8) ++nkeys;
-    return cudaSuccess;
-}
-
-template <typename T, bool SHADOW>
-static cudaError_t launch_wscan(const ScanArgs<T>& wrp, int G, const WscanPlan& P, cudaStream_t s)
-{
-    void (*fn)(ScanArgs<T>, int) = P.list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
-    fn<<<(unsigned)P.blocks, P.nc * G, P.smem, s>>>(wrp, P.nc);
-    return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
 {
@@ -688,18 +114,12 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
         ScanArgs<T> fun = A, rest = A;
         fun.naxes = rest.naxes = 0;
         rest.force = 1;
-        int mmax = 0;
         for (int k = 0; k < A.naxes; ++k) {
-            if (A.ax[k].m >= 2 && fscan_lanes<T>(A.ax[k].m) > 0) {
-                fun.ax[fun.naxes++] = A.ax[k];
-                mmax = max(mmax, A.ax[k].m);
-            } else {
-                rest.ax[rest.naxes++] = A.ax[k];
-            }
+            if (A.ax[k].m >= 2 && funnel_scan_fits<T>(A.ax[k].m)) fun.ax[fun.naxes++] = A.ax[k];
+            else rest.ax[rest.naxes++] = A.ax[k];
         }
         if (fun.naxes) {
-            const int G = fscan_lanes<T>(mmax);
-            cudaError_t e = A.shadow ? launch_fscan<T, true>(fun, G, mmax, s) : launch_fscan<T, false>(fun, G, mmax, s);
+            cudaError_t e = launch_funnel_scan<T>(fun, s);
             if (e != cudaSuccess) return e;
         }
         return rest.naxes ? launch_scan<T>(rest, s) : cudaSuccess;
@@ -712,9 +132,9 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
     thr.shadow = wrp.shadow = A.shadow;
     for (int k = 0; k < A.naxes; ++k) {
         const ScanAxis<T>& X = A.ax[k];
-        bool warp = X.m >= 64 && total <= 98304 && wscan_smem<T>(X.m, 1, 32, false) <= 200 * 1024;
+        bool warp = X.m >= 64 && total <= 98304 && lane_scan_fits<T>(X.m);
         if (A.force == 1) warp = false;
-        if (A.force >= 2) warp = X.m >= 2 && wscan_smem<T>(X.m, 1, 32, false) <= 200 * 1024;
+        if (A.force >= 2) warp = X.m >= 2 && lane_scan_fits<T>(X.m);
         if (warp) wrp.ax[wrp.naxes++] = X;
         else thr.ax[thr.naxes++] = X;
     }
@@ -738,27 +158,7 @@ cudaError_t launch_scan(ScanArgs<T> A, cudaStream_t s)
             if (e != cudaSuccess) return e;
         }
     }
-    if (wrp.naxes) {
-        int mmax = 0;
-        for (int k = 0; k < wrp.naxes; ++k) mmax = max(mmax, wrp.ax[k].m);
-        // automatic: pieces of about 16 elements (measured on 256^3 and 128^3
-        // grids and 1024^2 images: fewer pieces per chain do less speculative
-        // work, shorter ones keep more lanes busy)
-        int G = 32;
-        if (A.force == 0) while (G > 4 && mmax < 16 * G) G >>= 1;
-        else G = A.force == 3 ? 16 : A.force == 4 ? 8 : A.force == 5 ? 4 : 32;
-        if (wscan_chains<T>(mmax, G, false) == 0) G = 32;   // long chains: whole warps
-        WscanPlan P;
-        cudaError_t e = A.shadow ? wscan_plan<T, true>(wrp, G, mmax, P) : wscan_plan<T, false>(wrp, G, mmax, P);
-        if (e != cudaSuccess) return e;
-        int64_t blocks = 0;
-        for (int k = 0; k < wrp.naxes; ++k) {
-            wrp.ax[k].block_begin = blocks;
-            blocks += (wrp.ax[k].nchains + P.nc - 1) / P.nc;
-        }
-        if (blocks > 0)
-            return A.shadow ? launch_wscan<T, true>(wrp, G, P, s) : launch_wscan<T, false>(wrp, G, P, s);
-    }
+    if (wrp.naxes) return launch_lane_scan<T>(wrp, s);
     return cudaSuccess;
 }
 

@@ -201,6 +201,17 @@ cudaError_t launch_pad_weights(const ScanAxis<T>& X, T* ap, cudaStream_t s);
 // Chain prox by parametric min-cuts with message passing (mpprox.cu): one CTA
 // per chain, chains of at most kMpMaxLen elements.
 constexpr int kMpMaxLen = 2048;
+
+// Lane-group chain prox (lanescan.cu): G lanes per chain for launches with
+// few, long chains; the local form, or the funnel form for mapping 11.
+template <typename T>
+bool lane_scan_fits(int m);
+template <typename T>
+cudaError_t launch_lane_scan(ScanArgs<T> wrp, cudaStream_t s);
+template <typename T>
+bool funnel_scan_fits(int m);
+template <typename T>
+cudaError_t launch_funnel_scan(ScanArgs<T> fun, cudaStream_t s);
 template <typename T>
 cudaError_t launch_mp_prox(const ScanArgs<T>& A, cudaStream_t s);
 template <typename T>
