@@ -501,11 +501,24 @@ static void (*wscan_fn(int G))(ScanArgs<T>, int)
                   : wscan_kernel<T, SHADOW, 4, LIST>;
 }
 
-// Launch plan of the lane-group scan for G lanes per chain: with or without
+// Launch plan of the lane-group scan for G lanes per chain, with or without
 // the continuation lists (they spare phase 3 a second scan of every verified
-// continuation but take shared memory), whichever needs fewer waves of CTAs
-// over the GPU (the lists on a tie).  Occupancy comes from the runtime (the
-// kernels' registers and shared memory); plans are cached per shape.
+// continuation but take shared memory).  The two give the same results, so
+// the faster may be chosen by timing: from the third launch of a shape on,
+// two launches in every kTunePeriod (kTuneSlowPeriod once one form's mean is
+// at least 20% below the other's over 2 kTuneMin trials each) run one form
+// each between CUDA events on the caller's stream (the iterates change along
+// a solve, so the trials recur), the events are read without blocking at
+// later launches, and the other launches take the form with the lower mean
+// trial time once each form has kTuneMin trials.  Until then (and when the stream is being captured
+// into a graph, or an event fails) the lists are taken when they add no wave
+// work: their CTAs fit the GPU at once, or they need no more fractional
+// waves than the plain form.  What the
+// lists buy depends on the iterates, not the shape: per launch, lists against
+// plain, the 8-connected 1024^2 AAR (1.14x the waves) was 7% slower and its
+// FISTA 2% faster; uniform 2048^2 BCD (1.24x) 10% faster and its FISTA
+// (1.25x) 14% slower.  Occupancy comes from the runtime (the kernels'
+// registers and shared memory).  Plans are cached per shape.
 struct WscanPlan {
     bool list;
     int nc;
@@ -513,37 +526,77 @@ struct WscanPlan {
     size_t smem;
 };
 
-template <typename T, bool SHADOW>
-static cudaError_t wscan_plan(const ScanArgs<T>& wrp, int G, int mmax, WscanPlan& P)
+constexpr int kTuneSkip = 2;
+constexpr int kTunePeriod = 16;
+constexpr int kTuneSlowPeriod = 128;
+constexpr int kTuneMin = 3;
+constexpr int kTuneSlots = 8;          // event pairs in flight
+
+struct WscanEntry {
+    int dev, G, mmax, naxes;
+    int64_t nchains;
+    WscanPlan cand[2];
+    bool valid[2];
+    int rule;                          // form taken until both forms have kTuneMin trials
+    bool timing;                       // false: no timing (one form only, or an event failed)
+    int launches, trials;
+    cudaEvent_t ev0[kTuneSlots], ev1[kTuneSlots];
+    bool pending[kTuneSlots];
+    int var[kTuneSlots];
+    double sum[2];
+    int cnt[2];
+};
+
+static void wscan_entry_release(WscanEntry& E)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int64_t nchains = 0;
-    for (int k = 0; k < wrp.naxes; ++k) nchains += wrp.ax[k].nchains;
-    struct Key {
-        int dev, G, mmax, naxes;
-        int64_t nchains;
-    };
-    static Key keys[8];
-    static WscanPlan plans[8];
-    static int nkeys = 0, next = 0;
-    static std::mutex mu;                  // handles on other host threads share the cache
-    std::lock_guard<std::mutex> lock(mu);
-    for (int i = 0; i < nkeys; ++i)
-        if (keys[i].dev == dev && keys[i].G == G && keys[i].mmax == mmax && keys[i].naxes == wrp.naxes &&
-            keys[i].nchains == nchains) {
-            P = plans[i];
-            return cudaSuccess;
+    for (int t = 0; t < kTuneSlots; ++t) {
+        if (E.ev0[t]) cudaEventDestroy(E.ev0[t]);
+        if (E.ev1[t]) cudaEventDestroy(E.ev1[t]);
+        E.ev0[t] = E.ev1[t] = nullptr;
+        E.pending[t] = false;
+    }
+}
+
+// Reads the trials that have finished.  On an event error the timing stops
+// and the rule's form is kept.
+static void wscan_entry_poll(WscanEntry& E)
+{
+    if (!E.timing) return;
+    for (int t = 0; t < kTuneSlots; ++t) {
+        if (!E.pending[t]) continue;
+        const cudaError_t q = cudaEventQuery(E.ev1[t]);
+        if (q == cudaErrorNotReady) continue;
+        float ms = 0.f;
+        if (q != cudaSuccess || cudaEventElapsedTime(&ms, E.ev0[t], E.ev1[t]) != cudaSuccess) {
+            cudaGetLastError();
+            E.timing = false;
+            wscan_entry_release(E);
+            return;
         }
+        E.pending[t] = false;
+        E.sum[E.var[t]] += ms;
+        E.cnt[E.var[t]] += 1;
+    }
+}
+
+// The form for launches that are not trials.
+static int wscan_entry_form(const WscanEntry& E)
+{
+    if (!E.timing || E.cnt[0] < kTuneMin || E.cnt[1] < kTuneMin) return E.rule;
+    return E.sum[1] / E.cnt[1] <= E.sum[0] / E.cnt[0] ? 1 : 0;
+}
+
+template <typename T, bool SHADOW>
+static cudaError_t wscan_entry_make(const ScanArgs<T>& wrp, int G, int mmax, int dev, WscanEntry& E)
+{
     int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     static bool attr_set[64][4][2] = {};
     const int gi = G == 32 ? 0 : G == 16 ? 1 : G == 8 ? 2 : 3;
-    int64_t waves[2] = {-1, -1};
-    WscanPlan cand[2];
+    double waves[2] = {-1.0, -1.0};
     for (int li = 0; li < 2; ++li) {
+        E.valid[li] = false;
         const bool list = li == 1;
         const int nc = wscan_chains<T>(mmax, G, list);
         if (nc == 0) continue;
@@ -560,25 +613,105 @@ static cudaError_t wscan_plan(const ScanArgs<T>& wrp, int G, int mmax, WscanPlan
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nc * G, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) continue;
-        waves[li] = (blocks + (int64_t)per_sm * sms - 1) / ((int64_t)per_sm * sms);
-        cand[li] = WscanPlan{list, nc, blocks, smem};
+        waves[li] = (double)blocks / ((double)per_sm * sms);
+        E.cand[li] = WscanPlan{list, nc, blocks, smem};
+        E.valid[li] = true;
     }
-    if (waves[1] >= 0 && (waves[0] < 0 || waves[1] <= waves[0])) P = cand[1];
-    else if (waves[0] >= 0) P = cand[0];
-    else return cudaErrorInvalidConfiguration;
-    keys[next] = Key{dev, G, mmax, wrp.naxes, nchains};
-    plans[next] = P;
-    next = (next + 1) % 8;
-    if (nkeys < 8) ++nkeys;
+    if (!E.valid[0] && !E.valid[1]) return cudaErrorInvalidConfiguration;
+    const double allow = waves[0] > 1.0 ? waves[0] : 1.0;
+    E.rule = (E.valid[1] && (!E.valid[0] || waves[1] <= allow)) ? 1 : 0;
+    E.timing = E.valid[0] && E.valid[1];
+    E.launches = E.trials = 0;
+    for (int t = 0; t < kTuneSlots; ++t) {
+        E.ev0[t] = E.ev1[t] = nullptr;
+        E.pending[t] = false;
+        E.var[t] = 0;
+    }
+    E.sum[0] = E.sum[1] = 0.0;
+    E.cnt[0] = E.cnt[1] = 0;
     return cudaSuccess;
 }
 
+// Plans (and, for the first launches of a shape, times) one lane-group scan
+// launch and issues it.
 template <typename T, bool SHADOW>
-static cudaError_t launch_wscan(const ScanArgs<T>& wrp, int G, const WscanPlan& P, cudaStream_t s)
+static cudaError_t wscan_run(ScanArgs<T> wrp, int G, int mmax, cudaStream_t s)
 {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int64_t nchains = 0;
+    for (int k = 0; k < wrp.naxes; ++k) nchains += wrp.ax[k].nchains;
+    static WscanEntry cache[8];
+    static int nkeys = 0, next = 0;
+    static std::mutex mu;                  // handles on other host threads share the cache
+    std::lock_guard<std::mutex> lock(mu);
+    WscanEntry* E = nullptr;
+    for (int i = 0; i < nkeys; ++i) {
+        WscanEntry& c = cache[i];
+        if (c.dev == dev && c.G == G && c.mmax == mmax && c.naxes == wrp.naxes && c.nchains == nchains) E = &c;
+    }
+    if (!E) {
+        WscanEntry& c = cache[next];
+        if (next < nkeys) wscan_entry_release(c);
+        c.dev = dev;
+        c.G = G;
+        c.mmax = mmax;
+        c.naxes = wrp.naxes;
+        c.nchains = nchains;
+        e = wscan_entry_make<T, SHADOW>(wrp, G, mmax, dev, c);
+        if (e != cudaSuccess) return e;
+        E = &c;
+        next = (next + 1) % 8;
+        if (nkeys < 8) ++nkeys;
+    }
+    wscan_entry_poll(*E);
+    int form = wscan_entry_form(*E);
+    int slot = -1;
+    const bool clear = E->cnt[0] >= 2 * kTuneMin && E->cnt[1] >= 2 * kTuneMin &&
+                       (E->sum[0] / E->cnt[0] >= 1.2 * (E->sum[1] / E->cnt[1]) ||
+                        E->sum[1] / E->cnt[1] >= 1.2 * (E->sum[0] / E->cnt[0]));
+    const int phase = (E->launches - kTuneSkip) % (clear ? kTuneSlowPeriod : kTunePeriod);
+    if (E->timing && E->launches >= kTuneSkip && phase < 2) {
+        const int t = E->trials % kTuneSlots;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (!E->pending[t] && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            slot = t;
+            form = phase;
+        }
+        cudaGetLastError();
+    }
+    ++E->launches;
+    const WscanPlan P = E->cand[form];
+    int64_t blocks = 0;
+    for (int k = 0; k < wrp.naxes; ++k) {
+        wrp.ax[k].block_begin = blocks;
+        blocks += (wrp.ax[k].nchains + P.nc - 1) / P.nc;
+    }
+    if (blocks == 0) return cudaSuccess;
+    if (slot >= 0) {
+        if ((E->ev0[slot] || cudaEventCreate(&E->ev0[slot]) == cudaSuccess) &&
+            (E->ev1[slot] || cudaEventCreate(&E->ev1[slot]) == cudaSuccess) &&
+            cudaEventRecord(E->ev0[slot], s) == cudaSuccess) {
+            E->pending[slot] = true;
+            E->var[slot] = form;
+            ++E->trials;
+        } else {                           // no timing: keep the rule's form
+            cudaGetLastError();
+            E->timing = false;
+            wscan_entry_release(*E);
+            slot = -1;
+        }
+    }
     void (*fn)(ScanArgs<T>, int) = P.list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
     fn<<<(unsigned)P.blocks, P.nc * G, P.smem, s>>>(wrp, P.nc);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (slot >= 0 && E->pending[slot] && cudaEventRecord(E->ev1[slot], s) != cudaSuccess) {
+        cudaGetLastError();
+        E->timing = false;
+        wscan_entry_release(*E);
+    }
+    return e;
 }
 
 
@@ -604,16 +737,7 @@ cudaError_t launch_lane_scan(ScanArgs<T> wrp, cudaStream_t s)
     if (wrp.force == 0) while (G > 4 && mmax < 16 * G) G >>= 1;
     else G = wrp.force == 3 ? 16 : wrp.force == 4 ? 8 : wrp.force == 5 ? 4 : 32;
     if (wscan_chains<T>(mmax, G, false) == 0) G = 32;   // long chains: whole warps
-    WscanPlan P;
-    cudaError_t e = wrp.shadow ? wscan_plan<T, true>(wrp, G, mmax, P) : wscan_plan<T, false>(wrp, G, mmax, P);
-    if (e != cudaSuccess) return e;
-    int64_t blocks = 0;
-    for (int k = 0; k < wrp.naxes; ++k) {
-        wrp.ax[k].block_begin = blocks;
-        blocks += (wrp.ax[k].nchains + P.nc - 1) / P.nc;
-    }
-    if (blocks == 0) return cudaSuccess;
-    return wrp.shadow ? launch_wscan<T, true>(wrp, G, P, s) : launch_wscan<T, false>(wrp, G, P, s);
+    return wrp.shadow ? wscan_run<T, true>(wrp, G, mmax, s) : wscan_run<T, false>(wrp, G, mmax, s);
 }
 
 // Whether a chain of m elements fits the funnel lane-group scan.
