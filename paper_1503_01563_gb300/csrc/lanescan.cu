@@ -501,25 +501,30 @@ static void (*wscan_fn(int G))(ScanArgs<T>, int)
                   : wscan_kernel<T, SHADOW, 4, LIST>;
 }
 
-// Launch plan of the lane-group scan for G lanes per chain, with or without
-// the continuation lists (they spare phase 3 a second scan of every verified
-// continuation but take shared memory).  The two give the same results, so
-// the faster may be chosen by timing: from the third launch of a shape on,
-// two launches in every kTunePeriod (kTuneSlowPeriod once one form's mean is
-// at least 20% below the other's over 2 kTuneMin trials each) run one form
-// each between CUDA events on the caller's stream (the iterates change along
-// a solve, so the trials recur), the events are read without blocking at
-// later launches, and the other launches take the form with the lower mean
-// trial time once each form has kTuneMin trials.  Until then (and when the stream is being captured
-// into a graph, or an event fails) the lists are taken when they add no wave
-// work: their CTAs fit the GPU at once, or they need no more fractional
-// waves than the plain form.  What the
-// lists buy depends on the iterates, not the shape: per launch, lists against
-// plain, the 8-connected 1024^2 AAR (1.14x the waves) was 7% slower and its
-// FISTA 2% faster; uniform 2048^2 BCD (1.24x) 10% faster and its FISTA
-// (1.25x) 14% slower.  Occupancy comes from the runtime (the kernels'
-// registers and shared memory).  Plans are cached per shape.
+// Launch plan of the lane-group scan.  A launch shape has up to four forms:
+// G or G/2 lanes per chain (G from the automatic rule; a forced lane count
+// keeps one) and, for each, with or without the continuation lists (they
+// spare phase 3 a second scan of every verified continuation but take shared
+// memory).  All forms give the same results, and which is fastest depends on
+// the iterates, not only on the shape: per launch, on seg1024 AAR 16 lanes
+// took 180 us against 204 us for 32, while FISTA and BCD were 9% and 5%
+// faster with 32; lists against plain, seg1024 AAR 203 against 238 us and
+// FISTA 393 against 583 us, the 8-connected 1024^2 AAR 7% slower with them
+// and its FISTA 2% faster, uniform 2048^2 BCD 10% faster and its FISTA 14%
+// slower.  So the forms are timed: per launch shape, from the third launch
+// on, NF launches in every kTunePeriod (kTuneSlowPeriod once the fastest
+// form's mean is at least 20% below every other's over 2 kTuneMin trials
+// each) run one form each between CUDA events on the caller's stream (the
+// iterates change along a solve, so the trials recur); the events are read
+// without blocking at later launches, and the other launches take the form
+// with the lowest mean trial time once every form has kTuneMin trials.
+// Until then, and when the stream is being captured into a graph or an event
+// fails, G lanes with the lists if they add no wave work (their CTAs fit the
+// GPU at once, or they need no more fractional waves than the plain form).
+// Occupancy comes from the runtime (the kernels' registers and shared
+// memory).  Plans are cached per shape.
 struct WscanPlan {
+    int G;
     bool list;
     int nc;
     int64_t blocks;
@@ -531,20 +536,21 @@ constexpr int kTunePeriod = 16;
 constexpr int kTuneSlowPeriod = 128;
 constexpr int kTuneMin = 3;
 constexpr int kTuneSlots = 8;          // event pairs in flight
+constexpr int kMaxForms = 4;
 
 struct WscanEntry {
-    int dev, G, mmax, naxes;
+    int dev, G, mmax, naxes, force;
     int64_t nchains;
-    WscanPlan cand[2];
-    bool valid[2];
-    int rule;                          // form taken until both forms have kTuneMin trials
+    WscanPlan form[kMaxForms];
+    int nf;
+    int rule;                          // form taken until every form has kTuneMin trials
     bool timing;                       // false: no timing (one form only, or an event failed)
     int launches, trials;
     cudaEvent_t ev0[kTuneSlots], ev1[kTuneSlots];
     bool pending[kTuneSlots];
     int var[kTuneSlots];
-    double sum[2];
-    int cnt[2];
+    double sum[kMaxForms];
+    int cnt[kMaxForms];
 };
 
 static void wscan_entry_release(WscanEntry& E)
@@ -579,63 +585,87 @@ static void wscan_entry_poll(WscanEntry& E)
     }
 }
 
-// The form for launches that are not trials.
-static int wscan_entry_form(const WscanEntry& E)
+// The form for launches that are not trials, and whether it leads clearly.
+static int wscan_entry_form(const WscanEntry& E, bool& clear)
 {
-    if (!E.timing || E.cnt[0] < kTuneMin || E.cnt[1] < kTuneMin) return E.rule;
-    return E.sum[1] / E.cnt[1] <= E.sum[0] / E.cnt[0] ? 1 : 0;
+    clear = false;
+    if (!E.timing) return E.rule;
+    int best = -1;
+    for (int f = 0; f < E.nf; ++f) {
+        if (E.cnt[f] < kTuneMin) return E.rule;
+        if (best < 0 || E.sum[f] / E.cnt[f] < E.sum[best] / E.cnt[best]) best = f;
+    }
+    clear = true;
+    for (int f = 0; f < E.nf; ++f) {
+        if (f == best) continue;
+        if (E.cnt[f] < 2 * kTuneMin || E.cnt[best] < 2 * kTuneMin ||
+            E.sum[f] / E.cnt[f] < 1.2 * (E.sum[best] / E.cnt[best]))
+            clear = false;
+    }
+    return best;
 }
 
 template <typename T, bool SHADOW>
-static cudaError_t wscan_entry_make(const ScanArgs<T>& wrp, int G, int mmax, int dev, WscanEntry& E)
+static cudaError_t wscan_entry_make(const ScanArgs<T>& wrp, int G, bool halve, int mmax, int dev, WscanEntry& E)
 {
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     static bool attr_set[64][4][2] = {};
-    const int gi = G == 32 ? 0 : G == 16 ? 1 : G == 8 ? 2 : 3;
-    double waves[2] = {-1.0, -1.0};
-    for (int li = 0; li < 2; ++li) {
-        E.valid[li] = false;
-        const bool list = li == 1;
-        const int nc = wscan_chains<T>(mmax, G, list);
-        if (nc == 0) continue;
-        int64_t blocks = 0;
-        for (int k = 0; k < wrp.naxes; ++k) blocks += (wrp.ax[k].nchains + nc - 1) / nc;
-        const size_t smem = wscan_smem<T>(mmax, nc, G, list);
-        void (*fn)(ScanArgs<T>, int) = list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
-        if (dev < 0 || dev >= 64 || !attr_set[dev][gi][li]) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    E.nf = 0;
+    double waves_g[2] = {-1.0, -1.0};  // G lanes: plain, lists
+    int idx_g[2] = {-1, -1};
+    for (int gv = 0; gv < (halve && G > 4 ? 2 : 1); ++gv) {
+        const int g = gv ? G / 2 : G;
+        const int gi = g == 32 ? 0 : g == 16 ? 1 : g == 8 ? 2 : 3;
+        for (int li = 0; li < 2; ++li) {
+            const bool list = li == 1;
+            const int nc = wscan_chains<T>(mmax, g, list);
+            if (nc == 0) continue;
+            int64_t blocks = 0;
+            for (int k = 0; k < wrp.naxes; ++k) blocks += (wrp.ax[k].nchains + nc - 1) / nc;
+            const size_t smem = wscan_smem<T>(mmax, nc, g, list);
+            void (*fn)(ScanArgs<T>, int) = list ? wscan_fn<T, SHADOW, true>(g) : wscan_fn<T, SHADOW, false>(g);
+            if (dev < 0 || dev >= 64 || !attr_set[dev][gi][li]) {
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e != cudaSuccess) return e;
+                if (dev >= 0 && dev < 64) attr_set[dev][gi][li] = true;
+            }
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nc * g, smem);
             if (e != cudaSuccess) return e;
-            if (dev >= 0 && dev < 64) attr_set[dev][gi][li] = true;
+            if (per_sm < 1) continue;
+            if (gv == 0) {
+                waves_g[li] = (double)blocks / ((double)per_sm * sms);
+                idx_g[li] = E.nf;
+            }
+            E.form[E.nf++] = WscanPlan{g, list, nc, blocks, smem};
         }
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nc * G, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) continue;
-        waves[li] = (double)blocks / ((double)per_sm * sms);
-        E.cand[li] = WscanPlan{list, nc, blocks, smem};
-        E.valid[li] = true;
     }
-    if (!E.valid[0] && !E.valid[1]) return cudaErrorInvalidConfiguration;
-    const double allow = waves[0] > 1.0 ? waves[0] : 1.0;
-    E.rule = (E.valid[1] && (!E.valid[0] || waves[1] <= allow)) ? 1 : 0;
-    E.timing = E.valid[0] && E.valid[1];
+    if (E.nf == 0) return cudaErrorInvalidConfiguration;
+    const double allow = waves_g[0] > 1.0 ? waves_g[0] : 1.0;
+    if (idx_g[1] >= 0 && (idx_g[0] < 0 || waves_g[1] <= allow)) E.rule = idx_g[1];
+    else if (idx_g[0] >= 0) E.rule = idx_g[0];
+    else E.rule = 0;
+    E.timing = E.nf > 1;
     E.launches = E.trials = 0;
     for (int t = 0; t < kTuneSlots; ++t) {
         E.ev0[t] = E.ev1[t] = nullptr;
         E.pending[t] = false;
         E.var[t] = 0;
     }
-    E.sum[0] = E.sum[1] = 0.0;
-    E.cnt[0] = E.cnt[1] = 0;
+    for (int f = 0; f < kMaxForms; ++f) {
+        E.sum[f] = 0.0;
+        E.cnt[f] = 0;
+    }
     return cudaSuccess;
 }
 
-// Plans (and, for the first launches of a shape, times) one lane-group scan
-// launch and issues it.
+// Plans (and, on trial launches, times) one lane-group scan launch and
+// issues it.  G: lanes per chain of the automatic rule or the forced count;
+// halve: G/2 lanes are a candidate too.
 template <typename T, bool SHADOW>
-static cudaError_t wscan_run(ScanArgs<T> wrp, int G, int mmax, cudaStream_t s)
+static cudaError_t wscan_run(ScanArgs<T> wrp, int G, bool halve, int mmax, cudaStream_t s)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -647,32 +677,34 @@ static cudaError_t wscan_run(ScanArgs<T> wrp, int G, int mmax, cudaStream_t s)
     static std::mutex mu;                  // handles on other host threads share the cache
     std::lock_guard<std::mutex> lock(mu);
     WscanEntry* E = nullptr;
+    const int fkey = halve ? 1 : 0;
     for (int i = 0; i < nkeys; ++i) {
         WscanEntry& c = cache[i];
-        if (c.dev == dev && c.G == G && c.mmax == mmax && c.naxes == wrp.naxes && c.nchains == nchains) E = &c;
+        if (c.dev == dev && c.G == G && c.force == fkey && c.mmax == mmax && c.naxes == wrp.naxes &&
+            c.nchains == nchains)
+            E = &c;
     }
     if (!E) {
         WscanEntry& c = cache[next];
         if (next < nkeys) wscan_entry_release(c);
         c.dev = dev;
         c.G = G;
+        c.force = fkey;
         c.mmax = mmax;
         c.naxes = wrp.naxes;
         c.nchains = nchains;
-        e = wscan_entry_make<T, SHADOW>(wrp, G, mmax, dev, c);
+        e = wscan_entry_make<T, SHADOW>(wrp, G, halve, mmax, dev, c);
         if (e != cudaSuccess) return e;
         E = &c;
         next = (next + 1) % 8;
         if (nkeys < 8) ++nkeys;
     }
     wscan_entry_poll(*E);
-    int form = wscan_entry_form(*E);
+    bool clear = false;
+    int form = wscan_entry_form(*E, clear);
     int slot = -1;
-    const bool clear = E->cnt[0] >= 2 * kTuneMin && E->cnt[1] >= 2 * kTuneMin &&
-                       (E->sum[0] / E->cnt[0] >= 1.2 * (E->sum[1] / E->cnt[1]) ||
-                        E->sum[1] / E->cnt[1] >= 1.2 * (E->sum[0] / E->cnt[0]));
     const int phase = (E->launches - kTuneSkip) % (clear ? kTuneSlowPeriod : kTunePeriod);
-    if (E->timing && E->launches >= kTuneSkip && phase < 2) {
+    if (E->timing && E->launches >= kTuneSkip && phase < E->nf) {
         const int t = E->trials % kTuneSlots;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (!E->pending[t] && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
@@ -682,7 +714,7 @@ static cudaError_t wscan_run(ScanArgs<T> wrp, int G, int mmax, cudaStream_t s)
         cudaGetLastError();
     }
     ++E->launches;
-    const WscanPlan P = E->cand[form];
+    const WscanPlan P = E->form[form];
     int64_t blocks = 0;
     for (int k = 0; k < wrp.naxes; ++k) {
         wrp.ax[k].block_begin = blocks;
@@ -703,8 +735,8 @@ static cudaError_t wscan_run(ScanArgs<T> wrp, int G, int mmax, cudaStream_t s)
             slot = -1;
         }
     }
-    void (*fn)(ScanArgs<T>, int) = P.list ? wscan_fn<T, SHADOW, true>(G) : wscan_fn<T, SHADOW, false>(G);
-    fn<<<(unsigned)P.blocks, P.nc * G, P.smem, s>>>(wrp, P.nc);
+    void (*fn)(ScanArgs<T>, int) = P.list ? wscan_fn<T, SHADOW, true>(P.G) : wscan_fn<T, SHADOW, false>(P.G);
+    fn<<<(unsigned)P.blocks, P.nc * P.G, P.smem, s>>>(wrp, P.nc);
     e = cudaGetLastError();
     if (slot >= 0 && E->pending[slot] && cudaEventRecord(E->ev1[slot], s) != cudaSuccess) {
         cudaGetLastError();
@@ -737,7 +769,8 @@ cudaError_t launch_lane_scan(ScanArgs<T> wrp, cudaStream_t s)
     if (wrp.force == 0) while (G > 4 && mmax < 16 * G) G >>= 1;
     else G = wrp.force == 3 ? 16 : wrp.force == 4 ? 8 : wrp.force == 5 ? 4 : 32;
     if (wscan_chains<T>(mmax, G, false) == 0) G = 32;   // long chains: whole warps
-    return wrp.shadow ? wscan_run<T, true>(wrp, G, mmax, s) : wscan_run<T, false>(wrp, G, mmax, s);
+    const bool halve = wrp.force == 0;                 // automatic: G / 2 lanes are a candidate too
+    return wrp.shadow ? wscan_run<T, true>(wrp, G, halve, mmax, s) : wscan_run<T, false>(wrp, G, halve, mmax, s);
 }
 
 // Whether a chain of m elements fits the funnel lane-group scan.
