@@ -87,7 +87,11 @@ typedef struct {
                             that all loads coalesce), then one elementwise
                             update launch; the scan gives each chain a thread,
                             or, when there are too few chains to fill the GPU,
-                            a warp (speculative pieces, see csrc/scan.cu);
+                            a group of lanes (speculative pieces, see
+                            csrc/lanescan.cu: the lane count and the kernel
+                            form are chosen per launch shape by timing trial
+                            launches on the caller's stream, which never
+                            changes a result);
                             5: that schedule with thread-per-chain scans
                             forced; 6, 7, 8, 9: with 32, 16, 8 or 4 lanes per
                             chain (speculative pieces) forced; 10: the chain
