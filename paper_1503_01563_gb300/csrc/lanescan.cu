@@ -28,8 +28,9 @@ __device__ __forceinline__ void scan_cp_wait()
 //
 // For few, long chains (a 2D grid has only H + W of them) one thread per chain
 // leaves the GPU idle, so G lanes (4 .. 32, the kernel's template parameter)
-// share one chain: lane L scans piece L of G from a guessed state (a segment starts at the piece start with multiplier
-// 0; exact for lane 0) and records every bend it finds (position e and
+// share one chain: lane L scans piece L of G from a guessed state (a segment
+// starts at the piece start with multiplier 0; exact for lane 0) and records
+// every bend it finds (position e and
 // direction).  After a bend at e the scan state is fixed (the next segment
 // starts at e+1 with multiplier +-a_e), so a lane's trajectory is the true one
 // from the first bend it shares with the true scan.  Lane L then continues
@@ -39,9 +40,10 @@ __device__ __forceinline__ void scan_cp_wait()
 // exact, so following merges from lane 0 reaches the chain end through
 // verified lanes only; lanes not on that path are overwritten.  A launch
 // lasts as long as its slowest chain's critical path (piece, continuation,
-// rewrite); where shared memory allows it without another wave of CTAs,
-// each lane keeps its continuation's segments so that the rewrite only
-// stores them (the same values: the same scan from the same state).
+// rewrite); in the form with lists (LIST), each lane keeps its
+// continuation's segments so that the rewrite only stores them (the same
+// values: the same scan from the same state).  The launch plan below picks
+// the lane count and the form.
 
 // Advance one lane's scan through positions st.i .. stop-1 (data in shared
 // memory, skewed).  on_bend(s, e, d, t) is called for every finished segment
