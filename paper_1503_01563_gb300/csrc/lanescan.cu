@@ -701,7 +701,15 @@ static cudaError_t wscan_run(ScanArgs<T> wrp, int G, bool halve, int mmax, cudaS
         next = (next + 1) % 8;
         if (nkeys < 8) ++nkeys;
     }
-    wscan_entry_poll(*E);
+    {
+        // event queries are not allowed in a thread with a global-mode
+        // capture in progress; relaxed mode permits them and leaves it intact
+        cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+        const bool swapped = cudaThreadExchangeStreamCaptureMode(&mode) == cudaSuccess;
+        wscan_entry_poll(*E);
+        if (swapped) cudaThreadExchangeStreamCaptureMode(&mode);
+        cudaGetLastError();
+    }
     bool clear = false;
     int form = wscan_entry_form(*E, clear);
     int slot = -1;
