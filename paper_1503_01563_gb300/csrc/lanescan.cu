@@ -514,10 +514,11 @@ static void (*wscan_fn(int G))(ScanArgs<T>, int)
 // FISTA 393 against 583 us, the 8-connected 1024^2 AAR 7% slower with them
 // and its FISTA 2% faster, uniform 2048^2 BCD 10% faster and its FISTA 14%
 // slower.  So the forms are timed: per launch shape, from the third launch
-// on, NF launches in every kTunePeriod (kTuneSlowPeriod once the fastest
-// form's mean is at least 20% below every other's over 2 kTuneMin trials
-// each) run one form each between CUDA events on the caller's stream (the
-// iterates change along a solve, so the trials recur); the events are read
+// on, the first NF launches in every kTunePeriod run one form each between
+// CUDA events on the caller's stream (the iterates change along a solve, so
+// the trials recur); a form whose mean is at least 10% above the fastest
+// one's over 2 kTuneMin trials each is tried only once in kTuneSlowPeriod
+// launches, since a trial costs its gap to the fastest form; the events are read
 // without blocking at later launches, and the other launches take the form
 // with the lowest mean trial time once every form has kTuneMin trials.
 // Until then, and when the stream is being captured into a graph or an event
@@ -587,24 +588,24 @@ static void wscan_entry_poll(WscanEntry& E)
     }
 }
 
-// The form for launches that are not trials, and whether it leads clearly.
-static int wscan_entry_form(const WscanEntry& E, bool& clear)
+// The form for launches that are not trials (-1 when some form has too few
+// trials: the rule's form then).
+static int wscan_entry_best(const WscanEntry& E)
 {
-    clear = false;
-    if (!E.timing) return E.rule;
+    if (!E.timing) return -1;
     int best = -1;
     for (int f = 0; f < E.nf; ++f) {
-        if (E.cnt[f] < kTuneMin) return E.rule;
+        if (E.cnt[f] < kTuneMin) return -1;
         if (best < 0 || E.sum[f] / E.cnt[f] < E.sum[best] / E.cnt[best]) best = f;
     }
-    clear = true;
-    for (int f = 0; f < E.nf; ++f) {
-        if (f == best) continue;
-        if (E.cnt[f] < 2 * kTuneMin || E.cnt[best] < 2 * kTuneMin ||
-            E.sum[f] / E.cnt[f] < 1.2 * (E.sum[best] / E.cnt[best]))
-            clear = false;
-    }
     return best;
+}
+
+// Whether form f trails the fastest form far enough to be tried rarely.
+static bool wscan_entry_far(const WscanEntry& E, int best, int f)
+{
+    return best >= 0 && f != best && E.cnt[f] >= 2 * kTuneMin && E.cnt[best] >= 2 * kTuneMin &&
+           E.sum[f] / E.cnt[f] >= 1.1 * (E.sum[best] / E.cnt[best]);
 }
 
 template <typename T, bool SHADOW>
@@ -710,11 +711,13 @@ static cudaError_t wscan_run(ScanArgs<T> wrp, int G, bool halve, int mmax, cudaS
         if (swapped) cudaThreadExchangeStreamCaptureMode(&mode);
         cudaGetLastError();
     }
-    bool clear = false;
-    int form = wscan_entry_form(*E, clear);
+    const int best = wscan_entry_best(*E);
+    int form = best >= 0 ? best : E->rule;
     int slot = -1;
-    const int phase = (E->launches - kTuneSkip) % (clear ? kTuneSlowPeriod : kTunePeriod);
-    if (E->timing && E->launches >= kTuneSkip && phase < E->nf) {
+    const int64_t since = E->launches - kTuneSkip;
+    const int phase = (int)(since % kTunePeriod);
+    if (E->timing && since >= 0 && phase < E->nf &&
+        (!wscan_entry_far(*E, best, phase) || since % kTuneSlowPeriod < kTunePeriod)) {
         const int t = E->trials % kTuneSlots;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (!E->pending[t] && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
