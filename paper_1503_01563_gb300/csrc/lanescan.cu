@@ -508,12 +508,12 @@ static void (*wscan_fn(int G))(ScanArgs<T>, int)
 // keeps one) and, for each, with or without the continuation lists (they
 // spare phase 3 a second scan of every verified continuation but take shared
 // memory).  All forms give the same results, and which is fastest depends on
-// the iterates, not only on the shape: per launch, on seg1024 AAR 16 lanes
-// took 180 us against 204 us for 32, while FISTA and BCD were 9% and 5%
-// faster with 32; lists against plain, seg1024 AAR 203 against 238 us and
-// FISTA 393 against 583 us, the 8-connected 1024^2 AAR 7% slower with them
-// and its FISTA 2% faster, uniform 2048^2 BCD 10% faster and its FISTA 14%
-// slower.  So the forms are timed: per launch shape, from the third launch
+// the iterates, not only on the shape: per launch, on the 1024^2 blob
+// segmentation's AAR iterates 16 lanes took 180 us against 204 us for 32,
+// while its FISTA and BCD iterates ran 9% and 5% faster with 32; lists
+// against plain, that AAR 203 against 238 us and FISTA 393 against 583 us,
+// the 8-connected 1024^2 AAR 7% slower with them and its FISTA 2% faster,
+// uniform 2048^2 BCD 10% faster and its FISTA 14% slower.  So the forms are timed: per launch shape, from the third launch
 // on, the first NF launches in every kTunePeriod run one form each between
 // CUDA events on the caller's stream (the iterates change along a solve, so
 // the trials recur); a form whose mean is at least 10% above the fastest
