@@ -1098,7 +1098,7 @@ def run_ours(args):
                 methods[mname]["certified"] = {
                     "ms": float(np.median(times)), "iters": int(res.iters), "certified": bool(res.certified),
                     "energy_equals_oracle": bool(res.energy_i64 == e_star), "check_every": 2}
-    # the 2D segmentation (1024^2 blobs) on the same GPU, for the driver's record
+    # the 2D segmentation (1024^2 blobs) on the same GPU, recorded beside the main line
     seg = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar":
         seg = {"workload": "seg1024",
@@ -1109,7 +1109,7 @@ def run_ours(args):
                "fista": time_to_cut("seg1024", "fista", max(3, args.steps // 2), args.warmup, stream, flush),
                "fista_funnel": time_to_cut("seg1024", "fista", max(3, args.steps // 2), args.warmup, stream,
                                            flush, mapping=11)}
-    # the batch of 512 uneven grids (AAR), for the driver's record
+    # the batch of 512 uneven grids (AAR), recorded beside the main line
     batch = None
     if rank == 0 and args.workload == "volume256" and args.algo == "aar":
         import oracle
