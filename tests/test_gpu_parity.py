@@ -403,3 +403,35 @@ def test_lane_scan_forms_give_identical_states(tv, algo, dims):
         states.append(s.state())
         s.close()
     np.testing.assert_array_equal(states[0], states[1])
+
+
+def test_lane_scan_two_host_threads(tv):
+    """Two handles on their own streams, driven from two host threads at
+    once (the binding releases the interpreter lock in each call), share the
+    lane-group scan's per-shape plan and timing state: both end in the state
+    a solve alone reaches, bit for bit."""
+    import threading
+    dims = (787, 1021)
+    w, a = inputs.segmentation_problem(dims, 13)
+    wd, ad = dev(w), [dev(x) for x in a]
+
+    def solve(out, idx, stream):
+        s = tv.Solver(dims, algo=0, dtype=tv.F32, check_every=10 ** 6, stream=stream.cuda_stream)
+        s.set_problem(wd, ad)
+        for _ in range(25):
+            s.iterate(1)
+        torch.cuda.synchronize()
+        out[idx] = s.state()
+        s.close()
+
+    ref = [None]
+    solve(ref, 0, torch.cuda.Stream())
+    res = [None, None]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ts = [threading.Thread(target=solve, args=(res, i, streams[i])) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    np.testing.assert_array_equal(res[0], ref[0])
+    np.testing.assert_array_equal(res[1], ref[0])
